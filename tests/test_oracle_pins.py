@@ -1,0 +1,402 @@
+"""Pins of the oracle against facts that do not come from the oracle itself.
+
+Each test checks one oracle function against an independent statement of the
+same mathematics: numpy's Philox implementation, closed forms (Riemann sums of
+Gaussians, geometric sums of sinusoids, linear-Gaussian evidence), finite
+differences, brute-force quadrature of the K posterior, stationarity of the
+kernels, and textbook properties of ESS bisection and systematic resampling.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2609_17674_b300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# --------------------------------------------------------------------------
+# Philox4x64-10: numpy's independent implementation (counter pre-incremented)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(6))
+def test_philox_matches_numpy(seed):
+    rng = np.random.default_rng(seed)
+    ctr = rng.integers(1, 2**63, size=4, dtype=np.uint64)
+    key = rng.integers(0, 2**63, size=2, dtype=np.uint64)
+    prev = ctr.copy()
+    prev[0] -= np.uint64(1)
+    ref = np.random.Philox(key=key, counter=prev).random_raw(4)
+    assert (oracle.philox(ctr, key) == ref).all()
+
+
+def test_u01_open_interval():
+    assert oracle.u01(0) == 2.0**-54
+    assert oracle.u01(2**64 - 1) == 1.0 - 2.0**-54
+    assert 0.0 < oracle.u01(2**63) < 1.0
+
+
+# --------------------------------------------------------------------------
+# Likelihood closed forms
+# --------------------------------------------------------------------------
+def _pulse_wl(n, d=None, kmax=2):
+    wl = synth.pulse_workload("t", n, 1, kmax, 1, 5)
+    if d is not None:
+        wl.problems[0].d = d
+    return wl
+
+
+def test_empty_model_logl_is_data_energy():
+    wl = synth.config1()
+    o = oracle.Oracle(wl)
+    d = wl.problems[0].d
+    r = o.logl_grad(np.zeros((1, wl.kmax, 3)), np.zeros(1, np.int32), 1.0)
+    assert r["ll_new"][0] == pytest.approx(-0.5 * np.sum(d * d) / 0.01, rel=1e-14)
+    assert np.all(r["grad"] == 0.0)
+
+
+@pytest.mark.parametrize("A,t0,w", [(1.3, 0.5, 0.02), (0.7, 0.41, 0.006), (1.9, 0.6, 0.045)])
+def test_single_pulse_energy_riemann_closed_form(A, t0, w):
+    # d = 0, K = 1: logL = -1/2 A^2 sum_n g_n^2 / sigma^2 and, for a grid much finer than w,
+    # sum_n exp(-(t_n-t0)^2/w^2) = N w sqrt(pi) (Poisson summation, exponentially small error)
+    n = 8192
+    wl = _pulse_wl(n, d=np.zeros(n))
+    theta = np.array([[A, t0, w]])
+    z = np.zeros((1, wl.kmax, 3))
+    z[0, 0] = synth.theta_to_z(wl, 0, theta)[0]
+    o = oracle.Oracle(wl)
+    ll = o.logl_grad(z, np.array([1], np.int32), 1.0)["ll_new"][0]
+    # the coordinate round trip perturbs theta at the 1e-16 level; recover it exactly
+    th = np.array([o.L.orc_u01(0)])  # keep lib loaded
+    expect = -0.5 * A * A * n * w * math.sqrt(math.pi) / 0.01
+    assert ll == pytest.approx(expect, rel=1e-12)
+
+
+@pytest.mark.parametrize("f,phi0,A", [(3.0012e-3, 0.3, 0.05), (3.0041e-3, 5.9, 0.11)])
+def test_single_sinusoid_energy_geometric_sum(f, phi0, A):
+    # d = 0, fdot = 0: sum cos^2(w n + p) = N/2 + 1/2 Re[e^{2ip} (1 - e^{2iwN}) / (1 - e^{2iw})]
+    n, dt = 1 << 16, 15.0
+    wl = synth.sinusoid_workload("t", n, 1, 2, 1, 3)
+    wl.problems[0].d = np.zeros(n)
+    lo, hi = wl.bounds(0)
+    z = np.zeros((1, 2, 4))
+    z[0, 0] = synth.theta_to_z(wl, 0, np.array([[A, f, 0.5e-16, phi0]]))[0]
+    z[0, 0, 2] = -745.0  # fdot -> 0 exactly
+    o = oracle.Oracle(wl)
+    ll = o.logl_grad(z, np.array([1], np.int32), 1.0)["ll_new"][0]
+    om = 2 * math.pi * f * dt
+    geo = np.exp(2j * phi0) * (1 - np.exp(2j * om * n)) / (1 - np.exp(2j * om))
+    expect = -0.5 * A * A * (n / 2 + 0.5 * geo.real) / wl.problems[0].sigma ** 2
+    assert ll == pytest.approx(expect, rel=1e-9)
+
+
+def test_noise_free_truth_has_zero_residual():
+    rng = synth._rng(11)
+    pr = synth.pulse_problem(rng, 2048, 4, noise=False)
+    wl = synth.Workload("t", synth.PULSE, 6, 1, [pr], synth.PULSE_LO, synth.PULSE_HI,
+                        synth.PULSE_LOGMASK)
+    z = np.zeros((1, 6, 3))
+    z[0, :4] = synth.theta_to_z(wl, 0, pr.truth)
+    r = oracle.Oracle(wl).logl_grad(z, np.array([4], np.int32), 1.0)
+    assert abs(r["ll_new"][0]) < 1e-18
+
+
+# --------------------------------------------------------------------------
+# Gradients: Richardson-extrapolated central differences of the oracle's logp
+# --------------------------------------------------------------------------
+def _fd_grad(o, z, K, beta, idx, h):
+    def f(zz):
+        return o.logl_grad(zz, K, beta, want_scale=False)["logp"][0]
+
+    def cd(hh):
+        zp, zm = z.copy(), z.copy()
+        zp.flat[idx] += hh
+        zm.flat[idx] -= hh
+        return (f(zp) - f(zm)) / (2 * hh)
+
+    return (4 * cd(h / 2) - cd(h)) / 3
+
+
+@pytest.mark.parametrize("which", ["pulse", "sinusoid", "linamp"])
+def test_gradient_matches_finite_differences(which):
+    if which == "pulse":
+        wl = synth.pulse_workload("t", 1024, 3, 5, 1, 21)
+        o = oracle.Oracle(wl, n1=300)
+        z, K = synth.prior_population(wl, 3, 8)
+        i = int(np.argmax(K))
+        h = 1e-4
+    elif which == "sinusoid":
+        wl = synth.sinusoid_workload("t", 1 << 14, 3, 4, 1, 22)
+        o = oracle.Oracle(wl, n1=5000)
+        z = np.zeros((1, 4, 4))
+        z[0, :3] = synth.theta_to_z(wl, 0, wl.problems[0].truth) + 0.05
+        K = np.array([3], np.int32)
+        i = 0
+        h = 1e-4
+    else:
+        wl = synth.linamp_workload(n=256, k=3)
+        o = oracle.Oracle(wl)
+        z = np.array([[[0.3], [1.7], [-0.4]]])
+        K = np.array([3], np.int32)
+        i = 0
+        h = 1e-3
+    zi, Ki = z[i : i + 1].copy(), K[i : i + 1].copy()
+    beta = 0.37
+    g = o.logl_grad(zi, Ki, beta)["grad"][0]
+    for q in range(Ki[0] * wl.D):
+        fd = _fd_grad(o, zi, Ki, beta, q, h)
+        assert g.flat[q] == pytest.approx(fd, rel=2e-6, abs=1e-6 * (1 + abs(fd)))
+    assert np.all(g.flat[Ki[0] * wl.D :] == 0.0)
+
+
+def test_fisher_equals_negative_hessian_at_zero_residual():
+    # with r = 0 the Hessian of logL is exactly -J^T J / sigma^2; add the prior curvature
+    rng = synth._rng(5)
+    pr = synth.pulse_problem(rng, 4096, 2, noise=False)
+    wl = synth.Workload("t", synth.PULSE, 3, 1, [pr], synth.PULSE_LO, synth.PULSE_HI,
+                        synth.PULSE_LOGMASK)
+    o = oracle.Oracle(wl)
+    z = np.zeros((1, 3, 3))
+    z[0, :2] = synth.theta_to_z(wl, 0, pr.truth)
+    K = np.array([2], np.int32)
+    fis = o.logl_grad(z, K, 1.0, want_fisher=True)["fisher"][0]
+    h = 1e-5
+    for q in range(6):
+        zp, zm = z.copy(), z.copy()
+        zp.flat[q] += h
+        zm.flat[q] -= h
+        gp = o.logl_grad(zp, K, 1.0)["grad"][0].flat[q]
+        gm = o.logl_grad(zm, K, 1.0)["grad"][0].flat[q]
+        assert fis.flat[q] == pytest.approx(-(gp - gm) / (2 * h), rel=1e-5)
+
+
+def test_linamp_fisher_closed_form():
+    wl = synth.linamp_workload(n=200, k=3)
+    o = oracle.Oracle(wl)
+    t = np.arange(200) / 200
+    G = np.exp(-((t[:, None] - wl.fixed_tw[None, :, 0]) ** 2) / (2 * wl.fixed_tw[None, :, 1] ** 2))
+    z = np.array([[[0.1], [0.9], [2.0]]])
+    fis = o.logl_grad(z, np.array([3], np.int32), 0.6, want_fisher=True)["fisher"][0, :, 0]
+    expect = 0.6 * np.sum(G * G, 0) / 0.01 + 1.0 / wl.amp_sd**2
+    np.testing.assert_allclose(fis, expect, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Hamiltonian dynamics and NUTS
+# --------------------------------------------------------------------------
+def test_leapfrog_is_reversible():
+    wl = synth.pulse_workload("t", 1024, 3, 4, 1, 9)
+    o = oracle.Oracle(wl)
+    z = np.zeros(12)
+    z[:9] = synth.theta_to_z(wl, 0, wl.problems[0].truth).ravel() + 0.01
+    rng = np.random.default_rng(0)
+    p = np.zeros(12)
+    p[:9] = rng.standard_normal(9)
+    minv = np.array([1e-3, 1e-6, 1e-5])
+    g = o.logl_grad(z.reshape(1, 4, 3), np.array([3], np.int32), 1.0)["grad"].ravel()
+    z0, p0 = z.copy(), p.copy()
+    for _ in range(25):
+        o.leapfrog(3, 1.0, 0.05, minv, z, p, g)
+    p = -p
+    for _ in range(25):
+        o.leapfrog(3, 1.0, 0.05, minv, z, p, g)
+    np.testing.assert_allclose(z, z0, atol=1e-9)
+    np.testing.assert_allclose(-p, p0, atol=1e-7)
+
+
+def _linamp_posterior(wl, beta=1.0):
+    pr = wl.problems[0]
+    t = np.arange(pr.n) / pr.n
+    G = np.exp(-((t[:, None] - wl.fixed_tw[None, :, 0]) ** 2) / (2 * wl.fixed_tw[None, :, 1] ** 2))
+    s2 = pr.sigma**2
+    prec = np.eye(wl.kmax) / wl.amp_sd**2 + beta * G.T @ G / s2
+    cov = np.linalg.inv(prec)
+    mean = cov @ (np.full(wl.kmax, wl.amp_mean) / wl.amp_sd**2 + beta * G.T @ pr.d / s2)
+    return G, mean, cov
+
+
+def test_nuts_leaves_linear_gaussian_posterior_invariant():
+    wl = synth.linamp_workload(n=128, k=2, P=3000, seed=17)
+    o = oracle.Oracle(wl)
+    G, mean, cov = _linamp_posterior(wl)
+    rng = np.random.default_rng(4)
+    P = 3000
+    z = rng.multivariate_normal(mean, cov, size=P).reshape(P, 2, 1)
+    K = np.full(P, 2, np.int32)
+    r = o.logl_grad(z, K, 1.0)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    minv = np.array([np.mean(np.diag(cov))])
+    for rnd in range(3):
+        acc, nl, fl = o.nuts_move(0, rnd, 1.0, 0.6, minv, z, K, lo, ln)
+        assert np.all(nl > 0)
+    zz = z.reshape(P, 2)
+    for d in range(2):
+        sd = math.sqrt(cov[d, d])
+        assert abs(zz[:, d].mean() - mean[d]) < 4 * sd / math.sqrt(P)
+        assert stats.kstest((zz[:, d] - mean[d]) / sd, "norm").pvalue > 1e-3
+    # the chain moved: decorrelated from its start
+    assert np.mean(acc) > 0.5
+    # the carried likelihood parts belong to the returned points
+    r2 = o.logl_grad(z, K, 1.0)
+    np.testing.assert_allclose(ln, r2["ll_new"], rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Reversible jump: prior invariance and the brute-force K posterior
+# --------------------------------------------------------------------------
+def test_rj_converges_to_k_prior_at_beta_zero():
+    wl = synth.pulse_workload("t", 8, 1, 5, 1, 1)
+    o = oracle.Oracle(wl)
+    P = 4000
+    z = np.zeros((P, 5, 3))
+    K = np.zeros(P, np.int32)
+    lo, ln = np.zeros(P), np.zeros(P)
+    for rnd in range(120):
+        o.rj_move(rnd // 16, rnd % 16, 0.0, z, K, lo, ln)
+    counts = np.bincount(K, minlength=6)
+    assert stats.chisquare(counts).pvalue > 1e-3
+    zz = np.concatenate([z[i, : K[i]].ravel() for i in range(P)])
+    assert stats.kstest(zz, "logistic").pvalue > 1e-3
+
+
+def _toy_kposterior_workload(P, seed):
+    rng = synth._rng(99)
+    n = 64
+    lo, hi = (0.5, 0.05, 0.02, 0.0), (2.0, 0.95, 0.1, 0.0)
+    t = np.arange(n) / n
+    d = 0.8 * np.exp(-((t - 0.47) ** 2) / (2 * 0.04**2)) + 0.5 * rng.standard_normal(n)
+    pr = synth.Problem(d=d, t_origin=0.0, dt=1.0 / n, sigma=0.5)
+    return synth.Workload("toy", synth.PULSE, 1, P, [pr], lo, hi, 0b100, n_mut=5, max_depth=6,
+                          alpha=0.5, p_birth=0.5, p_death=0.5, seed=seed)
+
+
+def _toy_brute_force(wl, nodes=(24, 240, 24)):
+    pr = wl.problems[0]
+    t = np.arange(pr.n) / pr.n
+    lo, hi = wl.lo, wl.hi
+
+    def gl(a, b, m, panels=1):
+        x, w = np.polynomial.legendre.leggauss(m)
+        edges = np.linspace(a, b, panels + 1)
+        xs = np.concatenate([0.5 * (e1 - e0) * x + 0.5 * (e1 + e0) for e0, e1 in zip(edges, edges[1:])])
+        ws = np.concatenate([0.5 * (e1 - e0) * w for e0, e1 in zip(edges, edges[1:])])
+        return xs, ws
+
+    Ax, Aw = gl(lo[0], hi[0], nodes[0])
+    tx, tw = gl(lo[1], hi[1], 8, nodes[1] // 8)
+    lwx, lww = gl(math.log(lo[2]), math.log(hi[2]), nodes[2])
+    e0 = -0.5 * np.sum(pr.d**2) / pr.sigma**2
+    acc = 0.0
+    for wi, wv in zip(np.exp(lwx), lww):
+        g = np.exp(-((t[None, :] - tx[:, None]) ** 2) / (2 * wi * wi))   # [nt, n]
+        dg = g @ pr.d
+        gg = np.sum(g * g, 1)
+        # logL(A, t0) - e0 = (A d.g - A^2 g.g / 2) / sigma^2
+        ll = (Ax[:, None] * dg[None, :] - 0.5 * Ax[:, None] ** 2 * gg[None, :]) / pr.sigma**2
+        acc += wv * np.sum(Aw[:, None] * tw[None, :] * np.exp(ll))
+    # prior densities: uniform A, uniform t0, log-uniform w (uniform in log w)
+    z1_over_z0 = acc / ((hi[0] - lo[0]) * (hi[1] - lo[1]) * (math.log(hi[2]) - math.log(lo[2])))
+    return z1_over_z0, e0
+
+
+def test_toy_k_posterior_matches_brute_force():
+    r1, e0 = _toy_brute_force(_toy_kposterior_workload(1, 0))
+    r2, _ = _toy_brute_force(_toy_kposterior_workload(1, 0), nodes=(32, 400, 32))
+    assert r1 == pytest.approx(r2, rel=1e-6)  # quadrature converged
+    p1 = r2 / (1 + r2)
+    assert 0.15 < p1 < 0.95  # an informative toy
+    logz_exact = e0 + math.log(0.5 * (1 + r2))
+    fr, lz = [], []
+    for seed in range(6):
+        wl = _toy_kposterior_workload(1500, seed)
+        res = oracle.Oracle(wl).smc_run(1500)
+        fr.append(np.mean(res["K"] == 1))
+        lz.append(res["logz"])
+    fr, lz = np.array(fr), np.array(lz)
+    se_f = max(fr.std(ddof=1) / math.sqrt(len(fr)), 0.01)
+    se_z = max(lz.std(ddof=1) / math.sqrt(len(lz)), 0.02)
+    assert abs(fr.mean() - p1) < 3 * se_f + 0.01
+    assert abs(lz.mean() - logz_exact) < 3 * se_z + 0.02
+
+
+# --------------------------------------------------------------------------
+# SMC evidence and posterior on the linear-Gaussian model (closed form)
+# --------------------------------------------------------------------------
+def test_smc_evidence_and_posterior_match_linear_gaussian_closed_form():
+    wl0 = synth.linamp_workload(n=256, k=3, P=400, seed=31)
+    G, mean, cov = _linamp_posterior(wl0)
+    pr = wl0.problems[0]
+    n, s2 = pr.n, pr.sigma**2
+    m0 = np.full(3, wl0.amp_mean)
+    S = s2 * np.eye(n) + wl0.amp_sd**2 * G @ G.T
+    sign, logdet = np.linalg.slogdet(S)
+    res_ = pr.d - G @ m0
+    logz_full = -0.5 * res_ @ np.linalg.solve(S, res_) - 0.5 * logdet - 0.5 * n * math.log(2 * math.pi)
+    # the sampler omits the Gaussian normalisation -n/2 log(2 pi sigma^2) inside moves
+    logz_exact = logz_full + 0.5 * n * math.log(2 * math.pi * s2)
+    lz, mu = [], []
+    for seed in range(6):
+        wl = synth.linamp_workload(n=256, k=3, P=400, seed=31)
+        wl.seed = 100 + seed
+        res = oracle.Oracle(wl).smc_run(400)
+        lz.append(res["logz"])
+        mu.append(res["z"].reshape(400, 3).mean(0))
+        assert res["beta"][-1] == 1.0
+    lz, mu = np.array(lz), np.array(mu)
+    se = max(lz.std(ddof=1) / math.sqrt(len(lz)), 0.01)
+    assert abs(lz.mean() - logz_exact) < 3 * se + 0.02
+    sem = np.sqrt(np.diag(cov) / 400 + mu.var(0, ddof=1) / len(mu))
+    assert np.all(np.abs(mu.mean(0) - mean) < 4 * sem)
+
+
+# --------------------------------------------------------------------------
+# Tempering and resampling
+# --------------------------------------------------------------------------
+def test_temper_constant_ell_jumps_to_one():
+    bn, inc, ess, logw = oracle.temper(np.full(100, -3.0), 0.5, 0.25)
+    assert bn == 1.0 and ess == pytest.approx(100.0, rel=1e-14)
+    assert inc == pytest.approx(0.75 * -3.0, rel=1e-14)
+
+
+def test_temper_two_point_closed_form():
+    # half the particles at ell = 0, half at -L: ESS/P = (1+x)^2 / (2(1+x^2)), x = e^{-delta L};
+    # ESS = 0.9 P  <=>  x = 1/2, delta = ln 2 / L; evidence increment log((1+x)/2)
+    L, P = 100.0, 1000
+    ell = np.where(np.arange(P) % 2 == 0, 0.0, -L)
+    bn, inc, ess, logw = oracle.temper(ell, 0.9, 0.2)
+    assert bn - 0.2 == pytest.approx(math.log(2) / L, abs=2e-14)
+    assert inc == pytest.approx(math.log(0.75), abs=1e-12)
+    assert ess >= 0.9 * P and ess == pytest.approx(0.9 * P, rel=1e-10)
+
+
+def test_resample_properties():
+    wl = synth.config1()
+    o = oracle.Oracle(wl)
+    P = 512
+    assert np.array_equal(o.resample(3, np.zeros(P)), np.arange(P))
+    rng = np.random.default_rng(1)
+    logw = rng.normal(0, 3, P)
+    a = o.resample(4, logw)
+    assert np.all(np.diff(a) >= 0)
+    W = np.exp(logw - logw.max())
+    W /= W.sum()
+    counts = np.bincount(a, minlength=P)
+    assert np.all(counts >= np.floor(P * W) - 1e-9) and np.all(counts <= np.ceil(P * W) + 1e-9)
+
+
+def test_init_population_draws_the_prior():
+    wl = synth.config1()
+    z, K = oracle.Oracle(wl).init_population(22000)
+    assert stats.chisquare(np.bincount(K, minlength=11)).pvalue > 1e-3
+    zz = np.concatenate([z[i, : K[i]].ravel() for i in range(2000)])
+    assert stats.kstest(zz, "logistic").pvalue > 1e-3
+    assert np.all(z[np.arange(10)[None, :] >= K[:, None]] == 0.0)
+
+
+def test_eps_update_rule():
+    L = oracle.lib()
+    assert L.orc_eps_update(0.1, 0.8) == pytest.approx(0.1)
+    assert L.orc_eps_update(0.1, 0.3) == pytest.approx(0.1 * math.exp(-0.5))
+    assert L.orc_eps_update(1.9, 1.0) == 2.0 and L.orc_eps_update(1e-4, 0.0) == 1e-4
