@@ -1,0 +1,331 @@
+"""Benchmark: SMC stages of the transdimensional sampler on one B300 per rank.
+
+A step is one whole stage of the hot path (ESS bisection, reweight, systematic
+resampling, metric, then n_mut rounds of reversible-jump birth/death + NUTS)
+on the Gaussian-pulse workload at scale: N = 16384 samples, K_true = 20,
+K_max = 40, P = 8192 particles, mixed precision (FP32 templates and residuals,
+FP64 sums, anchors and log-weights).  The metric is component*sample logL+grad
+evaluations per second, counted on the device by the kernels themselves (the
+batched metric evaluation plus every NUTS leaf and initial point).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own independent problem (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "component*sample logL+grad evals/s"
+UNIT = "cs-evals/s"
+OPS_PER_CS = {0: 9.0, 1: 14.0}   # algorithmic FP32 lane-ops per component*sample (fwd+adj)
+FP32_LANES_PER_SM = 128
+N_SM = 148
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--particles", type=int, default=8192)
+    ap.add_argument("--samples", type=int, default=16384)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(rank: int, P: int, n: int):
+    from paper_2609_17674_b300 import synth
+
+    wl = synth.config2(seed=1002 + 1000 * rank, P=P, n=n)
+    return wl
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the oracle timed on a bounded sample (reference arm, cpu_baseline)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    """One oracle stage sample: metric on the slice, one RJ + NUTS round (oracle as is)."""
+    wl_seed, P, n, idx, stage, rnd = args
+    import oracle
+    from paper_2609_17674_b300 import synth
+
+    wl = synth.config2(seed=wl_seed, P=P, n=n)
+    o = oracle.Oracle(wl)
+    z, K = synth.prior_population(wl, 7)
+    z, K = z[idx].copy(), K[idx].copy()
+    t0 = time.perf_counter()
+    r = o.logl_grad(z, K, 1e-4, want_scale=False)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    minv = o.metric(z, K, 1e-4)
+    o.rj_move(stage, rnd, 1e-4, z, K, lo, ln)
+    Kn = K.copy()
+    acc, nl, fl = o.nuts_move(stage, rnd, 1e-4, o.eps_initial(), minv, z, K, lo, ln)
+    dt = time.perf_counter() - t0
+    cs = float(np.sum(K.astype(np.float64) * n)) * 2  # gradient eval + metric eval of the slice
+    cs += float(np.sum(Kn.astype(np.float64) * n * np.where(nl > 0, nl + 1, 0)))
+    return cs, dt
+
+
+def oracle_sample(wl_seed, P, n, cores, per_core, step):
+    import multiprocessing as mp
+
+    rng = np.random.default_rng(step)
+    idx = rng.choice(P, cores * per_core, replace=False)
+    jobs = [(wl_seed, P, n, idx[c * per_core:(c + 1) * per_core], step, 0) for c in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    cs = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return cs, wall, busy
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    per_core = 1
+    wl = workload(0, a.particles, a.samples)
+    for s in range(a.warmup):
+        oracle_sample(wl.seed, a.particles, a.samples, cores, per_core, 1000 + s)
+    tot_cs, tot_wall = 0.0, 0.0
+    for s in range(a.steps):
+        cs, wall, busy = oracle_sample(wl.seed, a.particles, a.samples, cores, per_core, s)
+        tot_cs += cs
+        tot_wall += busy
+    v = tot_cs / tot_wall
+    sample = (f"oracle (single-threaded FP64 C) per core: {per_core} particle(s) of the same "
+              f"workload, logL+grad + metric + one RJ move + one NUTS transition per step, "
+              f"{cores} processes")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_wall / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "N": a.samples, "P": a.particles, "kmax": 40,
+                   "K_true": 20, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200", "-i",
+                                       str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j]
+                          and "Not" not in r[5 + j]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(a):
+    import torch
+
+    from paper_2609_17674_b300 import capi, sampler
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def reduce(x, op):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    wl = workload(rank, a.particles, a.samples)
+    stream = torch.cuda.Stream()
+    ctx = sampler.open_context(wl, capi.MIXED, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ctx.init_population()
+    stage = 0
+    for _ in range(a.warmup):
+        ctx.run_stage(stage, use_graph=False)
+        stage += 1
+    ctx.profile(True)
+    ctx.counters(reset=True)
+    ctx.profile_read(reset=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    betas = []
+    for _ in range(a.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)          # L2 flush between steps (256 MB write)
+        b, lz, e = ctx.run_stage(stage, use_graph=False)
+        betas.append(float(b[0]))
+        stage += 1
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    (cs_eval, cs_nuts), launches = ctx.counters(reset=True)
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    ms_max = reduce(ms, dist.ReduceOp.MAX if dist else None)
+    cs_total = reduce(float(cs_eval + cs_nuts), dist.ReduceOp.SUM if dist else None)
+    value = cs_total / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (NUTS transition), ALU bound (FP32 pipe)
+    n_nuts, ms_nuts = prof["nuts"]
+    per_launch_ms = ms_nuts / max(n_nuts, 1)
+    ops = OPS_PER_CS[wl.model] * cs_nuts
+    achieved = ops / max(ms_nuts * 1e-3, 1e-12) / 1e12
+    mhz = clk.get("sm_mhz") or 2032.0
+    peak = FP32_LANES_PER_SM * N_SM * mhz * 1e6 / 1e12
+    roof = {"kernel": "k_nuts<PULSE,MIXED,32>", "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "Tops/s (FP32 lane-ops, FMA=1)", "frac": achieved / peak,
+            "traffic": None, "launches": n_nuts, "ms_per_launch": per_launch_ms,
+            "share_of_step": ms_nuts / ms, "peak_basis": f"128 FP32 lanes x 148 SMs x {mhz:.0f} MHz"
+                                                         " (median SM clock during the timed region)",
+            "kernels_ms": {k: v[1] for k, v in prof.items()}}
+
+    # end to end: population resident on the host between stages (pinned buffers)
+    e2e = None
+    if not a.no_e2e:
+        z, K, _, ln = ctx.get_population()
+        zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
+        Kh = torch.empty(K.shape, dtype=K.dtype, pin_memory=True)
+        lnh = torch.empty(ln.shape, dtype=ln.dtype, pin_memory=True)
+        zh.copy_(z)
+        Kh.copy_(K)
+        eps, _ = ctx.get_kernel_params()
+        beta_h = np.array([betas[-1]])
+        logz_h = np.zeros(1)
+        zd, Kd = torch.empty_like(z), torch.empty_like(K)
+        nsteps = max(2, a.steps // 2)
+        ctx.counters(reset=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            with torch.cuda.stream(stream):
+                zd.copy_(zh, non_blocking=True)
+                Kd.copy_(Kh, non_blocking=True)
+            ctx.set_population(zd, Kd, beta=beta_h, logz=logz_h)
+            ctx.set_kernel_params(eps)
+            b, lz, _ = ctx.run_stage(stage, use_graph=True)
+            stage += 1
+            zo, Ko, _, lno = ctx.get_population()
+            with torch.cuda.stream(stream):
+                zh.copy_(zo, non_blocking=True)
+                Kh.copy_(Ko, non_blocking=True)
+                lnh.copy_(lno, non_blocking=True)
+            eps, _ = ctx.get_kernel_params()
+            stream.synchronize()
+            beta_h, logz_h = b, lz
+        t1 = time.perf_counter()
+        barrier()
+        (ce, cn), _ = ctx.counters(reset=True)
+        el = reduce(t1 - t0, dist.ReduceOp.MAX if dist else None)
+        cst = reduce(float(ce + cn), dist.ReduceOp.SUM if dist else None)
+        h2d = zh.numel() * 8 + Kh.numel() * 4 + 8 * 4
+        d2h = zh.numel() * 8 + Kh.numel() * 4 + lnh.numel() * 8 + 8 * 5
+        e2e = {"value": cst / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "path": "pinned host population -> tsmc_set_population -> tsmc_run_stage (graph)"
+                       " -> tsmc_get_population -> pinned host"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not a.no_cpu:
+        cores = len(os.sched_getaffinity(0))
+        cs, wall, busy = oracle_sample(wl.seed, a.particles, a.samples, cores, 1, 0)
+        cpu = {"value": cs / busy, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{cores} particles of the same workload (one per core, {cores} "
+                         "processes): logL+grad, metric, one RJ move and one NUTS transition "
+                         f"each; {busy:.1f} s"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name + " (SMC stage: ESS bisection, resampling, metric, "
+                                         "5 x [RJ birth/death + NUTS depth<=6])",
+                   "N": a.samples, "P": a.particles, "kmax": 40, "K_true": 20,
+                   "precision": "mixed: FP32 templates/residuals, FP64 sums/anchors/log-weights",
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"{world} independent problem(s), one per GPU",
+                   "stages": [stage - a.steps - (max(2, a.steps // 2) if e2e else 0), stage],
+                   "beta_end": betas[-1]},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * tsmc.h -- C ABI of the B300 transdimensional SMC library (libtsmc.so).
+ *
+ * Method: Demasi & Del Pozzo, "Massively parallel transdimensional sampling
+ * with data assimilation".  A population of particles (k, theta_k) moves from
+ * the prior (or from a previous posterior) to the posterior through tempered
+ * bridges (Sec. 2, Eqs. prior_bridge / reuse_bridge); each stage reweights
+ * (Eq. incremental_weight), picks beta by ESS bisection (Eqs. ess, ess_target),
+ * resamples and mutates with a mixture of NUTS and reversible-jump birth/death
+ * kernels (Eq. kernel_mixture, Sec. 3.1-3.2, Sec. 4).
+ *
+ * Conventions
+ *   - Every pointer argument named *_dev is CUDA device memory of the current
+ *     device; *_host is host memory.  The caller owns every buffer.  The
+ *     library never allocates device memory: all state lives in the workspace
+ *     the caller passes to tsmc_create.
+ *   - Coordinates z are FP64, row-major [n_problems * P][kmax][D], unconstrained
+ *     (logit) coordinates; D = 3 (pulse: A, t0, w), 4 (sinusoid: A, f, fdot,
+ *     phi0), 1 (linear-amplitude test model).  Rows k >= K_p are ignored on
+ *     input and written as zero.
+ *   - Particle index = problem * P + local index.
+ *   - All calls are ordered on the stream given to tsmc_create.  Calls that
+ *     return host values synchronise that stream; the others are asynchronous.
+ *   - Errors: argument errors return TSMC_EINVAL synchronously; CUDA launch
+ *     errors return TSMC_ECUDA.  A non-finite target density is not an error
+ *     (it means probability zero: the move is rejected / the subtree diverges).
+ *     tsmc_last_error gives a one-line message for the last failure.
+ *   - One context per host thread; contexts are independent.
+ */
+#ifndef TSMC_H
+#define TSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TSMC_OK = 0,
+  TSMC_EINVAL = -1,     /* bad argument (sizes, null pointers, non-finite data) */
+  TSMC_ENOMEM = -2,     /* workspace smaller than tsmc_workspace_bytes */
+  TSMC_ECUDA = -3,      /* a CUDA call or kernel launch failed */
+  TSMC_ENONFINITE = -4, /* non-finite value in host data */
+  TSMC_ETIMEOUT = -5,   /* reserved: a bounded device wait ran out */
+  TSMC_ESTATE = -6      /* call out of order (e.g. moves before data) */
+} tsmc_status;
+
+typedef enum { TSMC_PULSE = 0, TSMC_SINUSOID = 1, TSMC_PULSE_LINAMP = 2 } tsmc_model;
+typedef enum { TSMC_FP64 = 0, TSMC_MIXED = 1 } tsmc_precision;
+typedef enum { TSMC_SCHED_ROUNDS = 0, TSMC_SCHED_MIXTURE = 1 } tsmc_schedule;
+
+typedef struct {
+  int32_t model;          /* tsmc_model */
+  int32_t precision;      /* tsmc_precision: FP64 everywhere, or FP32 templates/residuals */
+  int32_t schedule;       /* ROUNDS: each round one RJ move then one NUTS transition;
+                             MIXTURE: each round each particle draws NUTS/birth/death
+                             with p_nuts/p_birth/p_death (Eq. kernel_mixture) */
+  int32_t n_problems;     /* independent data sets sharing one launch */
+  int32_t particles;      /* P, particles per problem */
+  int32_t kmax;           /* maximum component count (LINAMP: the fixed count) */
+  int32_t n_mut;          /* mutation rounds per stage */
+  int32_t max_depth;      /* NUTS maximum tree depth (<= 10) */
+  double alpha;           /* ESS target fraction, Eq. ess_target */
+  double p_nuts, p_birth, p_death;  /* Eq. kernel_mixture; p_birth=p_death=0.5 in ROUNDS */
+  double amp_mean, amp_sd;          /* LINAMP Gaussian amplitude prior */
+  uint64_t seed;          /* Philox4x64-10 key word 0 (word 1 = problem index) */
+  int32_t threads;        /* threads per particle block; 0 picks a default per model */
+  int32_t samples_per_thread;  /* mixed path register tile: 0 (default 32), 16 or 32 */
+} tsmc_config;
+
+/* Workspace size for a configuration and per-problem sample capacities
+ * n_capacity_host[n_problems] (the largest N each problem will hold, including
+ * assimilated samples).  The workspace must be 256-byte aligned device memory. */
+tsmc_status tsmc_workspace_bytes(const tsmc_config* cfg, const int64_t* n_capacity_host,
+                                 size_t* bytes);
+
+/* Creates a context over a caller-owned workspace; cuda_stream is a cudaStream_t
+ * (NULL: legacy default stream).  The context keeps pointers into the workspace,
+ * which must outlive it. */
+tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* n_capacity_host,
+                        void* workspace_dev, size_t bytes, void* cuda_stream, void** ctx_out);
+tsmc_status tsmc_destroy(void* ctx);
+const char* tsmc_last_error(const void* ctx);
+
+/* Data of one problem: samples d_n (host FP64, n <= capacity) on the grid
+ * t_n = t_origin + n*dt with white noise sigma; per-parameter prior bounds
+ * lo/hi (theta = lo + (hi-lo) s(z), or log-uniform where bit d of logmask is
+ * set).  All samples count as new (n1 = 0).  Copies to the device. */
+tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, int64_t n,
+                             double t_origin, double dt, double sigma, const double* lo_host,
+                             const double* hi_host, uint32_t logmask);
+
+/* LINAMP only: fixed (t0, w) per component, host [kmax][2]. */
+tsmc_status tsmc_set_fixed_components(void* ctx, const double* tw_host);
+
+/* Prior start (Sec. 4 step 1): K ~ U{0..kmax}, z ~ logistic (theta from its prior);
+ * beta = 0, log Z = 0, step size eps_0 = 0.5 (kmax D)^(-1/4), unit metric. */
+tsmc_status tsmc_init_population(void* ctx);
+
+/* Posterior start / resume: population from device arrays, beta and log Z per problem. */
+tsmc_status tsmc_set_population(void* ctx, const double* z_dev, const int32_t* K_dev,
+                                const double* beta_host, const double* logz_host);
+/* Copies the population out (any output may be NULL). */
+tsmc_status tsmc_get_population(void* ctx, double* z_dev, int32_t* K_dev, double* ll_old_dev,
+                                double* ll_new_dev);
+
+/* Batched logL + adjoint gradient (hot path) over caller arrays for all
+ * n_problems*P particles, each with its own K_p and its problem's data:
+ *   r_n = d_n - sum_{k<K} h(t_n; theta_k)
+ *   ll_old = -1/2 sum_{n<n1} r_n^2/sigma^2, ll_new = -1/2 sum_{n>=n1} r_n^2/sigma^2
+ *   logp = ll_old + beta_p * ll_new + log prior(z)
+ *   grad = d logp / dz   ([P][kmax][D], zero rows beyond K)
+ *   fisher = per-particle sum over components of the Gauss-Newton diagonal
+ *            sum_n c_n (dh/dz_d)^2/sigma^2 + prior curvature, [P][D]
+ * beta_dev[n_problems] (NULL: the context's current beta).  Any output may be NULL
+ * except ll_new_dev; grad and fisher cost a second pass over the samples. */
+tsmc_status tsmc_eval_logl_grad(void* ctx, const double* z_dev, const int32_t* K_dev,
+                                const double* beta_dev, double* ll_old_dev, double* ll_new_dev,
+                                double* logp_dev, double* grad_dev, double* fisher_dev);
+
+/* Reversible-jump birth/death move on the context population (Sec. 3.1):
+ * birth proposes one component from its prior, death removes a uniform one;
+ * log alpha = dL_c + log p_death - log p_birth (birth) or its mirror (death),
+ * dL_c from the incremental change (r.h - h.h/2)/sigma^2 (birth) or
+ * -(r.h + h.h/2)/sigma^2 (death) with per-sample temperatures.  Random numbers
+ * use (stage, round).  outcome_dev[P_total] (nullable): 0 no move, 1/2 birth/death
+ * accepted, -1/-2 rejected. */
+tsmc_status tsmc_rj_move(void* ctx, int32_t stage, int32_t round, int32_t* outcome_dev);
+
+/* One NUTS transition per particle (Sec. 3.2) with the context's step size and
+ * diagonal metric.  acc_dev (mean min(1, e^{H0-H}) over leaves), nleaf_dev,
+ * flags_dev (bit0 divergence, bits 8-15 depth) are nullable [P_total] outputs. */
+tsmc_status tsmc_nuts_move(void* ctx, int32_t stage, int32_t round, double* acc_dev,
+                           int32_t* nleaf_dev, int32_t* flags_dev);
+
+/* Step size and inverse diagonal metric per problem: eps_host[n_problems],
+ * minv_host[n_problems][D]. */
+tsmc_status tsmc_set_kernel_params(void* ctx, const double* eps_host, const double* minv_host);
+tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_host, double* minv_host);
+
+/* Metric from the population (Sec. 3.2, mass matrix = Hessian of -log target):
+ * minv_d = 1 / max(1e-8, mean over particles and active components of the
+ * Gauss-Newton diagonal at the current beta). */
+tsmc_status tsmc_update_metric(void* ctx);
+
+/* Choose beta by ESS bisection, reweight (evidence increment) and resample
+ * systematically (Sec. 2 steps 1-2).  Host outputs (nullable) [n_problems]. */
+tsmc_status tsmc_temper_reweight_resample(void* ctx, int32_t stage, double* beta_host,
+                                          double* logz_host, double* ess_host);
+/* Ancestors of the last resampling, [P_total] local indices (test access). */
+tsmc_status tsmc_get_ancestors(void* ctx, int32_t* anc_dev);
+
+/* One whole stage: temper/reweight/resample, metric, n_mut mutation rounds,
+ * step-size update eps <- eps exp(mean_acc - 0.8) clamped to [1e-4, 2].
+ * Problems already at beta = 1 before the stage are skipped.  Host outputs
+ * (nullable) [n_problems].  Uses a CUDA graph for the mutation rounds when
+ * use_graph != 0. */
+tsmc_status tsmc_run_stage(void* ctx, int32_t stage, int32_t use_graph, double* beta_host,
+                           double* logz_host, double* ess_host);
+
+/* Data assimilation (Eq. reuse_bridge, Sec. 5.1-5.2 posterior start): append
+ * n_new samples to a problem, mark them new (n1 = old n), recompute each
+ * particle's logL on the new samples and restart that problem's beta at 0.
+ * The evidence accumulator restarts at 0 (it then estimates log Z(d2)/Z(d1)). */
+tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new_host, int64_t n_new);
+
+/* Philox4x64-10 (the library's random stream) on the device: out_dev[4*i..4*i+3]
+ * = Philox(ctr_dev[4*i..4*i+3], {key0, key1}) for i < n. */
+tsmc_status tsmc_philox(void* ctx, const uint64_t* ctr_dev, uint64_t key0, uint64_t key1,
+                        int64_t n, uint64_t* out_dev);
+
+/* Statistics (no counterpart in the paper's method; measurement support):
+ * cs_evals_host[2] = component*sample logL+grad evaluations done by this context's
+ * kernels, the sum of K_p * N over every gradient evaluation: [0] batched
+ * evaluations with a gradient, [1] NUTS (every leaf plus the initial point);
+ * launches_host = kernels launched.  reset != 0 zeroes both after reading.
+ * Synchronises the stream. */
+tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_host,
+                          int32_t reset);
+
+/* Per-kernel-class event timing of eager launches (graphs are not used while it is
+ * on).  Classes: 0 eval, 1 rj, 2 nuts, 3 temper, 4 resample, 5 gather, 6 metric,
+ * 7 other.  tsmc_profile_read fills launches_host[8] and ms_host[8] (device time
+ * between events recorded on the context stream around each launch) and
+ * synchronises the stream; reset != 0 forgets the records. */
+tsmc_status tsmc_profile(void* ctx, int32_t enable);
+tsmc_status tsmc_profile_read(void* ctx, int64_t* launches_host, double* ms_host, int32_t reset);
+
+/* Waits for the stream; returns TSMC_ECUDA with a message on an asynchronous error. */
+tsmc_status tsmc_sync(void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

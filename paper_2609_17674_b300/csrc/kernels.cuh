@@ -1,0 +1,748 @@
+// kernels.cuh -- the sampler's kernels: batched evaluation, reversible-jump
+// birth/death, NUTS transitions, prior initialisation, ESS tempering,
+// systematic resampling and the population metric.
+#pragma once
+#include "likelihood.cuh"
+
+namespace tsmc {
+
+// Everything a population kernel needs, passed by value.
+struct KParams {
+  const ProbDev* probs;
+  int32_t n_problems, P, kmax, D, model, schedule, max_depth, n_mut;
+  double p_nuts, p_birth, p_death;
+  PriorArgs pa;
+  uint64_t seed;
+  const double* tw;          // LINAMP fixed (t0, w), [kmax][2]
+  double* z;                 // [Ptot][kmax][D]
+  int32_t* K;                // [Ptot]
+  double* ll_old;            // [Ptot]
+  double* ll_new;            // [Ptot]
+  const double* beta;        // [n_problems]
+  const double* eps;         // [n_problems]
+  const double* minv;        // [n_problems][4]
+  const int32_t* stage;      // device stage counter (graph-stable)
+  unsigned long long* cs_count;  // component*sample logL+grad evaluations (statistic)
+};
+
+// Shared-memory carve for one particle block.
+struct SmemPlan {
+  int kd;          // kmax * D
+  int nw;          // warps per block
+  int depth;       // NUTS checkpoint levels (0 for non-NUTS kernels)
+  bool fisher;
+  __host__ __device__ size_t eval_bytes() const {
+    return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4) +
+           sizeof(float) * (size_t)kd * NCF + 16;
+  }
+  __host__ __device__ size_t nuts_bytes() const {
+    return sizeof(double) * (size_t)kd * (13 + 2 * (size_t)(depth + 1));
+  }
+  // eval kernel: + gradient and Gauss-Newton staging; RJ: + proposal coordinates
+  __host__ __device__ size_t eval_kernel_bytes() const {
+    return eval_bytes() + 2 * sizeof(double) * (size_t)kd + 64;
+  }
+  __host__ __device__ size_t rj_kernel_bytes() const {
+    return eval_bytes() + sizeof(double) * (size_t)(kd + 4) + 64;
+  }
+  __host__ __device__ size_t nuts_kernel_bytes() const { return eval_bytes() + nuts_bytes() + 64; }
+};
+
+__device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, const double* tw) {
+  EvalSmem sm;
+  double* d = reinterpret_cast<double*>(p);
+  sm.th = d; d += sp.kd;
+  sm.dth = d; d += sp.kd;
+  sm.pg = d; d += sp.kd;
+  sm.pc = d; d += sp.kd;
+  sm.wacc = d; d += (size_t)sp.nw * sp.kd;
+  if (sp.fisher) { sm.wfis = d; d += (size_t)sp.nw * sp.kd; } else { sm.wfis = nullptr; }
+  sm.red = d; d += 128;
+  sm.scal = d; d += 4;
+  sm.cf = reinterpret_cast<float*>(d);
+  p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kd * NCF);
+  // keep 8-byte alignment for what follows
+  p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+  sm.tw = tw;
+  return sm;
+}
+
+// ---------------------------------------------------------------------------
+// Batched evaluation: one block per particle (caller arrays).
+// ---------------------------------------------------------------------------
+struct EvalIO {
+  const double* z; const int32_t* K; const double* beta;
+  double* ll_old; double* ll_new; double* logp; double* grad; double* fis_sum;
+};
+
+template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
+__global__ void __launch_bounds__(512) k_eval(KParams kp, EvalIO io, SmemPlan sp) {
+  extern __shared__ __align__(16) char smem[];
+  constexpr int D = model_d<MODEL>();
+  const int64_t gi = blockIdx.x;
+  const int prob = (int)(gi / kp.P);
+  const ProbDev pb = kp.probs[prob];
+  char* p = smem;
+  EvalSmem sm = carve_eval(p, sp, kp.tw);
+  double* gbuf = reinterpret_cast<double*>(p);   // [kd] gradient staging
+  double* fbuf = gbuf + sp.kd;                  // [kd] Gauss-Newton staging
+  const int K = min(max(io.K[gi], 0), kp.kmax);   // caller array: clamp to the slots
+  const double beta = io.beta[prob];
+  const double* z = io.z + gi * (int64_t)sp.kd;
+  block_eval<MODEL, PREC, R, GRAD, FISHER>(pb, kp.pa, K, beta, z, sm, gbuf, fbuf);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    if (io.ll_old) io.ll_old[gi] = sm.scal[1];
+    io.ll_new[gi] = sm.scal[2];
+    if (io.logp) io.logp[gi] = sm.scal[0];
+  }
+  if (GRAD && io.grad) {
+    double* g = io.grad + gi * (int64_t)sp.kd;
+    for (int i = tid; i < sp.kd; i += blockDim.x) g[i] = i < K * D ? gbuf[i] : 0.0;
+  }
+  if (GRAD && tid == 0 && kp.cs_count)
+    atomicAdd(kp.cs_count, (unsigned long long)K * (unsigned long long)pb.n);   // slot 0: batched
+  if (FISHER && io.fis_sum) {
+    if (tid < D) {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += fbuf[k * D + tid];
+      io.fis_sum[gi * D + tid] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Prior initialisation: one thread per particle.
+// ---------------------------------------------------------------------------
+__global__ void k_init(KParams kp, int64_t Ptot) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= Ptot) return;
+  const int prob = (int)(gi / kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P);
+  const int kd = kp.kmax * kp.D;
+  double* z = kp.z + gi * kd;
+  for (int j = 0; j < kd; ++j) z[j] = 0.0;
+  if (kp.model == PULSE_LINAMP) {
+    kp.K[gi] = kp.kmax;
+    for (int j = 0; j < kp.kmax; ++j)
+      z[j] = kp.pa.amp_mean +
+             kp.pa.amp_sd * draw_normal(kp.seed, prob, li, 0, 0, PU_INIT, 4 + (uint64_t)j);
+    return;
+  }
+  Rand4 w = draw(kp.seed, prob, li, 0, 0, PU_INIT, 0);
+  int k = (int)floor(__dmul_rn(u01(w.w[0]), (double)(kp.kmax + 1)));
+  if (k > kp.kmax) k = kp.kmax;
+  kp.K[gi] = k;
+  for (int j = 0; j < k * kp.D; ++j) {
+    if ((j & 3) == 0) w = draw(kp.seed, prob, li, 0, 0, PU_INIT, 1 + (uint64_t)(j >> 2));
+    const double u = u01(w.w[j & 3]);
+    z[j] = log(u) - log1p(-u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reversible-jump birth/death: one block per particle (Sec. 3.1 nested map).
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC, int R>
+__global__ void __launch_bounds__(512) k_rj(KParams kp, int round, int32_t* outcome, SmemPlan sp) {
+  extern __shared__ __align__(16) char smem[];
+  constexpr int D = model_d<MODEL>();
+  __shared__ int s_move;       // 0 none, 1 birth, 2 death
+  __shared__ int s_j;
+  __shared__ double s_u;
+  __shared__ double s_znew[4];
+  const int64_t gi = blockIdx.x;
+  const int prob = (int)(gi / kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P);
+  const ProbDev pb = kp.probs[prob];
+  if (pb.done) return;
+  const int stage = *kp.stage;
+  const int K = min(max(kp.K[gi], 0), kp.kmax);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int move = 0;
+    const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_RJ, 0);
+    bool birth;
+    bool active = kp.model != PULSE_LINAMP;
+    if (active && kp.schedule == 1) {
+      const Rand4 m = draw(kp.seed, prob, li, stage, round, PU_MOVETYPE, 0);
+      const double um = u01(m.w[0]);
+      active = !(um < kp.p_nuts);
+      birth = um < kp.p_nuts + kp.p_birth;
+    } else {
+      birth = u01(w.w[0]) < kp.p_birth / (kp.p_birth + kp.p_death);
+    }
+    int out = 0;
+    if (active) {
+      if (birth && K >= kp.kmax) out = -1;
+      else if (!birth && K <= 0) out = -2;
+      else move = birth ? 1 : 2;
+    }
+    if (move == 1) {
+      const Rand4 pw = draw(kp.seed, prob, li, stage, round, PU_RJPARAM, 0);
+      for (int d = 0; d < D; ++d) {
+        const double u = u01(pw.w[d]);
+        s_znew[d] = log(u) - log1p(-u);
+      }
+    } else if (move == 2) {
+      int j = (int)floor(__dmul_rn(u01(w.w[2]), (double)K));
+      if (j >= K) j = K - 1;
+      s_j = j;
+    }
+    s_u = u01(w.w[1]);
+    s_move = move;
+    if (move == 0 && outcome) outcome[gi] = out;
+  }
+  __syncthreads();
+  const int move = s_move;
+  if (move == 0) return;
+  char* p = smem;
+  EvalSmem sm = carve_eval(p, sp, kp.tw);
+  double* zs = reinterpret_cast<double*>(p);    // [kd + D]
+  const double* zg = kp.z + gi * (int64_t)sp.kd;
+  for (int i = tid; i < K * D; i += blockDim.x) zs[i] = zg[i];
+  if (move == 1 && tid < D) zs[K * D + tid] = s_znew[tid];
+  __syncthreads();
+  const int kp_idx = move == 1 ? K : s_j;      // index of the proposed component
+  eval_setup<MODEL, PREC>(pb, kp.pa, move == 1 ? K + 1 : K, zs, sm);
+  const int64_t N = pb.n, n1 = pb.n1;
+  double a_old = 0.0, a_new = 0.0;
+  const int64_t seg = (int64_t)blockDim.x * R;
+  const int warp = tid >> 5;
+  for (int64_t base = 0; base < N; base += seg) {
+    if (base + (int64_t)warp * 32 * R >= N) continue;
+    const int64_t m = base + (int64_t)tid * R;
+    if (PREC == MIXED) {
+      float r[R], hp[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
+      const float mf = (float)m;
+      for (int k = 0; k < K; ++k) {
+        float h[R];
+        mixed_vals<MODEL, R>(sm.cf + k * NCF, mf, h);
+#pragma unroll
+        for (int j = 0; j < R; ++j) r[j] -= h[j];
+      }
+      mixed_vals<MODEL, R>(sm.cf + kp_idx * NCF, mf, hp);
+      float so = 0.f, sn = 0.f;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t n = m + j;
+        const float h = n < N ? hp[j] : 0.0f;
+        const float t = move == 1 ? __fmaf_rn(-0.5f * h, h, r[j] * h)
+                                  : -__fmaf_rn(0.5f * h, h, r[j] * h);
+        if (n < n1) so += t; else sn += t;
+      }
+      a_old += (double)so;
+      a_new += (double)sn;
+    } else {
+      double hs[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) hs[j] = 0.0;
+      for (int k = 0; k < K; ++k) {
+        const double* th = sm.th + k * D;
+        const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
+        const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), nullptr));
+      }
+      const double* thp = sm.th + kp_idx * D;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t n = m + j;
+        if (n >= N) continue;
+        const double r = __dadd_rn(pb.d64[n], -hs[j]);
+        const double h = fp64_val<MODEL>(thp, 0.0, 0.0, time_of(pb, n), nullptr);
+        const double rh = __dmul_rn(r, h), hh = __dmul_rn(__dmul_rn(0.5, h), h);
+        const double t = move == 1 ? __dadd_rn(rh, -hh) : -__dadd_rn(rh, hh);
+        if (n < n1) a_old += t; else a_new += t;
+      }
+    }
+  }
+  double v[2] = {a_old, a_new};
+  block_sum<2>(v, sm.red);
+  if (tid == 0) {
+    const double d_old = v[0] * pb.inv_s2, d_new = v[1] * pb.inv_s2;
+    const double beta = kp.beta[prob];
+    const double dl = d_old + beta * d_new;
+    const double la = move == 1 ? dl + log(kp.p_death) - log(kp.p_birth)
+                                : dl + log(kp.p_birth) - log(kp.p_death);
+    int out;
+    double* zw = kp.z + gi * (int64_t)sp.kd;
+    if (log(s_u) < la) {
+      if (move == 1) {
+        for (int d = 0; d < D; ++d) zw[K * D + d] = s_znew[d];
+        kp.K[gi] = K + 1;
+        out = 1;
+      } else {
+        const int j = s_j;
+        for (int d = 0; d < D; ++d) {
+          zw[j * D + d] = zw[(K - 1) * D + d];
+          zw[(K - 1) * D + d] = 0.0;
+        }
+        kp.K[gi] = K - 1;
+        out = 2;
+      }
+      kp.ll_old[gi] += d_old;
+      kp.ll_new[gi] += d_new;
+    } else {
+      out = move == 1 ? -1 : -2;
+    }
+    if (outcome) outcome[gi] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NUTS transition: one block per particle.  Warp 0 runs the tree logic on the
+// (K*D)-vectors in shared memory; every leapfrog calls the block-wide
+// evaluation.  Control values are broadcast through shared memory.
+// ---------------------------------------------------------------------------
+struct NutsOut { double* acc; int32_t* nleaf; int32_t* flags; };
+
+__device__ __forceinline__ double warp_dot_minv(const double* a, const double* b,
+                                                const double* minv, int n, int D) {
+  double s = 0.0;
+  for (int i = threadIdx.x & 31; i < n; i += 32) s += a[i] * (minv[i % D] * b[i]);
+  return warp_sum(s);
+}
+
+template <int MODEL, int PREC, int R>
+__global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
+  extern __shared__ __align__(16) char smem[];
+  constexpr int D = model_d<MODEL>();
+  __shared__ int s_flag[4];          // 0: subtree valid, 1: stop, 2: direction
+  __shared__ double s_ctl[8];
+  const int64_t gi = blockIdx.x;
+  const int prob = (int)(gi / kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P);
+  const ProbDev pb = kp.probs[prob];
+  if (pb.done) return;
+  const int stage = *kp.stage;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = min(max(kp.K[gi], 0), kp.kmax);
+  const int n = K * D;
+  bool run = n > 0;
+  if (kp.schedule == 1) {
+    const Rand4 m = draw(kp.seed, prob, li, stage, round, PU_MOVETYPE, 0);
+    run = run && (u01(m.w[0]) < kp.p_nuts);
+  }
+  if (!run) {
+    if (tid == 0) {
+      if (out.acc) out.acc[gi] = 0.0;
+      if (out.nleaf) out.nleaf[gi] = 0;
+      if (out.flags) out.flags[gi] = 0;
+    }
+    return;
+  }
+  char* p = smem;
+  EvalSmem sm = carve_eval(p, sp, kp.tw);
+  double* v = reinterpret_cast<double*>(p);
+  const int kd = sp.kd;
+  double *zc = v, *z1 = v + kd, *p1 = v + 2 * kd, *g1 = v + 3 * kd;
+  double *zL = v + 4 * kd, *pL = v + 5 * kd, *gL = v + 6 * kd;
+  double *zR = v + 7 * kd, *pR = v + 8 * kd, *gR = v + 9 * kd;
+  double *rho = v + 10 * kd, *srho = v + 11 * kd, *sz = v + 12 * kd;
+  double* ckp = v + 13 * kd;                  // [(depth+1)][kd]
+  double* ckr = ckp + (size_t)(sp.depth + 1) * kd;
+  const double beta = kp.beta[prob];
+  const double eps = kp.eps[prob];
+  const double* minv = kp.minv + 4 * prob;
+  const double* zg = kp.z + gi * (int64_t)kd;
+  for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
+  __syncthreads();
+  block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+  // control state (meaningful in warp 0)
+  double H0 = 0, logW = 0, sum_acc = 0, cand_lo = 0, cand_ln = 0, sub_logW = 0, sub_lo = 0,
+         sub_ln = 0;
+  int leaves = 0, diverged = 0, depth_done = 0;
+  if (warp == 0) {
+    const double logp0 = sm.scal[0];
+    cand_lo = sm.scal[1];
+    cand_ln = sm.scal[2];
+    for (int i = lane; i < n; i += 32) {
+      const double pm = sqrt(1.0 / minv[i % D]) *
+                        draw_normal(kp.seed, prob, li, stage, round, PU_MOMENTUM, (uint64_t)i);
+      pL[i] = pm; pR[i] = pm; rho[i] = pm;
+      zL[i] = zc[i]; zR[i] = zc[i];
+      gL[i] = g1[i]; gR[i] = g1[i];
+    }
+    __syncwarp();
+    double kin = 0.0;
+    for (int i = lane; i < n; i += 32) kin += minv[i % D] * pL[i] * pL[i];
+    kin = warp_sum(kin);
+    H0 = -logp0 + 0.5 * kin;
+    logW = -H0;
+  }
+  for (int depth = 0; depth < kp.max_depth; ++depth) {
+    const int nsub = 1 << depth;
+    if (warp == 0) {
+      int dir = 0;
+      if (lane == 0) {
+        const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_DIRECTION, (uint64_t)depth);
+        dir = u01(w.w[0]) < 0.5 ? -1 : 1;
+      }
+      dir = __shfl_sync(0xffffffffu, dir, 0);
+      const double *zs0 = dir > 0 ? zR : zL, *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
+      for (int i = lane; i < n; i += 32) {
+        z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0.0;
+      }
+      sub_logW = -INFINITY;
+      if (lane == 0) { s_flag[0] = 1; s_flag[2] = dir; }
+    }
+    __syncthreads();
+    const double de = s_flag[2] * eps;
+    bool valid = true;
+    for (int l = 0; l < nsub; ++l) {
+      if (warp == 0) {
+        for (int i = lane; i < n; i += 32) {
+          const double ph = p1[i] + 0.5 * de * g1[i];
+          p1[i] = ph;
+          z1[i] = z1[i] + de * minv[i % D] * ph;
+        }
+      }
+      __syncthreads();
+      block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+      if (warp == 0) {
+        double kin = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          const double pn = p1[i] + 0.5 * de * g1[i];
+          p1[i] = pn;
+          kin += minv[i % D] * pn * pn;
+        }
+        kin = warp_sum(kin);
+        const double H = -sm.scal[0] + 0.5 * kin;
+        const int leaf_id = (nsub - 1) + l;
+        ++leaves;
+        if (isfinite(H)) { const double a = exp(H0 - H); sum_acc += a < 1.0 ? a : 1.0; }
+        int ok = 1;
+        if (!isfinite(H) || H - H0 > 1000.0) {
+          ok = 0;
+          diverged = 1;
+        } else {
+          const double lw = -H;
+          const double nl = logaddexp(sub_logW, lw);
+          int take = (l == 0);
+          if (!take) {
+            int t = 0;
+            if (lane == 0) {
+              const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_LEAF, (uint64_t)leaf_id);
+              t = u01(w.w[0]) < exp(lw - nl);
+            }
+            take = __shfl_sync(0xffffffffu, t, 0);
+          }
+          if (take) {
+            for (int i = lane; i < n; i += 32) sz[i] = z1[i];
+            sub_lo = sm.scal[1];
+            sub_ln = sm.scal[2];
+          }
+          sub_logW = nl;
+          for (int mm = 1; mm <= depth; ++mm) {
+            if ((l & ((1 << mm) - 1)) == 0) {
+              for (int i = lane; i < n; i += 32) {
+                ckp[mm * kd + i] = p1[i];
+                ckr[mm * kd + i] = srho[i];
+              }
+            }
+          }
+          for (int i = lane; i < n; i += 32) srho[i] += p1[i];
+          __syncwarp();
+          for (int mm = 1; mm <= depth && ok; ++mm) {
+            if (((l + 1) & ((1 << mm) - 1)) == 0) {
+              double s1 = 0.0, s2 = 0.0;
+              for (int i = lane; i < n; i += 32) {
+                const double seg = srho[i] - ckr[mm * kd + i];
+                const double mi = minv[i % D];
+                s1 += seg * (mi * ckp[mm * kd + i]);
+                s2 += seg * (mi * p1[i]);
+              }
+              s1 = warp_sum(s1);
+              s2 = warp_sum(s2);
+              if (s1 <= 0.0 || s2 <= 0.0) ok = 0;
+            }
+          }
+        }
+        if (lane == 0) s_flag[0] = ok;
+      }
+      __syncthreads();
+      valid = s_flag[0] != 0;
+      if (!valid) break;
+    }
+    if (!valid) break;
+    if (warp == 0) {
+      const int dir = s_flag[2];
+      double *ze = dir > 0 ? zR : zL, *pe = dir > 0 ? pR : pL, *ge = dir > 0 ? gR : gL;
+      for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = g1[i]; }
+      int take = 0;
+      if (lane == 0) {
+        const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_TOP, (uint64_t)depth);
+        take = u01(w.w[0]) < exp(sub_logW - logW);
+      }
+      take = __shfl_sync(0xffffffffu, take, 0);
+      if (take) {
+        for (int i = lane; i < n; i += 32) zc[i] = sz[i];
+        cand_lo = sub_lo;
+        cand_ln = sub_ln;
+      }
+      logW = logaddexp(logW, sub_logW);
+      for (int i = lane; i < n; i += 32) rho[i] += srho[i];
+      __syncwarp();
+      depth_done = depth + 1;
+      const double dl = warp_dot_minv(rho, pL, minv, n, D);
+      const double dr = warp_dot_minv(rho, pR, minv, n, D);
+      if (lane == 0) s_flag[1] = (dl <= 0.0 || dr <= 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_flag[1]) break;
+  }
+  if (warp == 0) {
+    double* zw = kp.z + gi * (int64_t)kd;
+    for (int i = lane; i < n; i += 32) zw[i] = zc[i];
+    if (lane == 0) {
+      kp.ll_old[gi] = cand_lo;
+      kp.ll_new[gi] = cand_ln;
+      if (out.acc) out.acc[gi] = leaves > 0 ? sum_acc / leaves : 0.0;
+      if (out.nleaf) out.nleaf[gi] = leaves;
+      if (out.flags) out.flags[gi] = diverged | (depth_done << 8);
+      if (kp.cs_count)   // slot 1: NUTS (initial point + every leaf)
+        atomicAdd(kp.cs_count + 1, (unsigned long long)n / D * (unsigned long long)pb.n *
+                                       (unsigned long long)(leaves + 1));
+    }
+  }
+  (void)s_ctl;
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive tempering (one block per problem): ESS(delta) = (sum x)^2 / sum x^2 with
+// x_i = exp(delta (ell_i - max ell)); bisection for ESS = alpha P on (0, 1-beta].
+// ---------------------------------------------------------------------------
+struct TemperIO {
+  const double* ell;   // ll_new [Ptot]
+  double* logw;        // [Ptot]
+  double* beta;        // [n_problems] in/out
+  double* logz;        // [n_problems] in/out
+  double* ess;         // [n_problems]
+  ProbDev* probs;      // done flags
+  double alpha;
+};
+
+__device__ void ess_sums(const double* ell, int P, double m, double delta, double* red,
+                         double& s1, double& s2) {
+  double v[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double e = ell[i];
+    const double x = isfinite(e) ? exp(delta * (e - m)) : 0.0;
+    v[0] += x;
+    v[1] += x * x;
+  }
+  block_sum<2>(v, red);
+  s1 = v[0];
+  s2 = v[1];
+}
+
+__global__ void __launch_bounds__(1024) k_temper(TemperIO io, int P) {
+  __shared__ double red[128];
+  __shared__ double s_m;
+  const int prob = blockIdx.x;
+  const double* ell = io.ell + (int64_t)prob * P;
+  double* logw = io.logw + (int64_t)prob * P;
+  const double beta = io.beta[prob];
+  if (beta >= 1.0) {
+    if (threadIdx.x == 0) io.probs[prob].done = 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) logw[i] = 0.0;
+    return;
+  }
+  double mx = -INFINITY;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double e = ell[i];
+    if (isfinite(e) && e > mx) mx = e;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    s_m = m;
+  }
+  __syncthreads();
+  const double m = s_m;
+  const double target = io.alpha * (double)P;
+  const double dmax = 1.0 - beta;
+  double s1, s2;
+  ess_sums(ell, P, m, dmax, red, s1, s2);
+  double delta;
+  bool to_one = false;
+  if (s1 * s1 / s2 >= target) {
+    delta = dmax;
+    to_one = true;
+  } else {
+    double lo = 0.0, hi = dmax;
+    for (int it = 0; it < 100; ++it) {
+      if (hi - lo < 1e-14) break;
+      const double mid = 0.5 * (lo + hi);
+      ess_sums(ell, P, m, mid, red, s1, s2);
+      if (s1 * s1 / s2 >= target) lo = mid; else hi = mid;
+    }
+    delta = lo > 0.0 ? lo : hi;
+    ess_sums(ell, P, m, delta, red, s1, s2);
+  }
+  for (int i = threadIdx.x; i < P; i += blockDim.x) logw[i] = delta * ell[i];
+  if (threadIdx.x == 0) {
+    io.beta[prob] = to_one ? 1.0 : beta + delta;
+    io.logz[prob] += (delta * m + log(s1)) - log((double)P);
+    io.ess[prob] = s1 * s1 / s2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Systematic resampling (one block per problem): FP64 inclusive scan of
+// W_i = exp(logw_i - max), U from Philox, a_i = min{j : C_j > (i+U)/P C_P}.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_resample(const double* logw_all, double* cw_all,
+                                                   int32_t* anc_all, const ProbDev* probs,
+                                                   uint64_t seed, int stage, int P) {
+  __shared__ double red[128];
+  __shared__ double s_carry[33];
+  __shared__ double s_m;
+  const int prob = blockIdx.x;
+  if (probs[prob].done) return;
+  const double* logw = logw_all + (int64_t)prob * P;
+  double* C = cw_all + (int64_t)prob * P;
+  int32_t* anc = anc_all + (int64_t)prob * P;
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double mx = -INFINITY;
+  for (int i = tid; i < P; i += T) mx = logw[i] > mx ? logw[i] : mx;
+  mx = warp_max(mx);
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = -INFINITY;
+    for (int w = 0; w < (T >> 5); ++w) m = red[w] > m ? red[w] : m;
+    s_m = m;
+  }
+  __syncthreads();
+  const double m = s_m;
+  // contiguous chunk per thread, sequential local scan, then block exclusive scan
+  const int chunk = (P + T - 1) / T;
+  const int b = tid * chunk, e = min(P, b + chunk);
+  double run = 0.0;
+  for (int i = b; i < e; ++i) { run += exp(logw[i] - m); C[i] = run; }
+  // exclusive scan of per-thread totals across the block
+  double x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  double excl = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) excl = 0.0;
+  if (lane == 31) s_carry[warp] = x;
+  __syncthreads();
+  if (tid == 0) {
+    double c = 0.0;
+    for (int w = 0; w < (T >> 5); ++w) { const double t = s_carry[w]; s_carry[w] = c; c += t; }
+    s_carry[32] = c;
+  }
+  __syncthreads();
+  const double off = s_carry[warp] + excl;
+  for (int i = b; i < e; ++i) C[i] += off;
+  __syncthreads();
+  const double total = C[P - 1];
+  const Rand4 w = draw(seed, prob, 0, stage, 0, PU_RESAMPLE, 0);
+  const double U = u01(w.w[0]);
+  for (int i = tid; i < P; i += T) {
+    const double target = ((double)i + U) / (double)P * total;
+    int lo = 0, hi = P - 1;    // first j with C_j > target (C_{P-1} = total > target)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (C[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    anc[i] = lo;
+  }
+}
+
+// gather the population rows of the ancestors into the alternate buffers
+__global__ void k_gather(const int32_t* anc, const ProbDev* probs, int P, int kd,
+                         const double* z, const int32_t* K, const double* lo, const double* ln,
+                         double* z2, int32_t* K2, double* lo2, double* ln2, int64_t Ptot) {
+  const int64_t total = Ptot * (kd + 1);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / (kd + 1);
+    const int c = (int)(t % (kd + 1));
+    const int prob = (int)(i / P);
+    const int64_t src = probs[prob].done ? i : (int64_t)prob * P + anc[i];
+    if (c < kd) z2[i * kd + c] = z[src * kd + c];
+    else { K2[i] = K[src]; lo2[i] = lo[src]; ln2[i] = ln[src]; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Metric and step size (one block per problem)
+// ---------------------------------------------------------------------------
+__global__ void k_metric(const double* fis_sum, const int32_t* K, const ProbDev* probs, int P,
+                         int D, double* minv) {
+  __shared__ double red[160];
+  const int prob = blockIdx.x;
+  if (probs[prob].done) return;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int64_t g = (int64_t)prob * P + i;
+    for (int d = 0; d < D; ++d) v[d] += fis_sum[g * D + d];
+    v[4] += (double)K[g];
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 4; ++d) {
+      double h = (d < D && v[4] > 0.0) ? v[d] / v[4] : 1.0;
+      if (!(h > 1e-8)) h = 1e-8;
+      minv[4 * prob + d] = 1.0 / h;
+    }
+  }
+}
+
+// per-round acceptance statistics: stats[prob] += (sum acc over moved, count)
+__global__ void k_round_stats(const double* acc, const int32_t* nleaf, const ProbDev* probs,
+                              int P, double* stats) {
+  __shared__ double red[64];
+  const int prob = blockIdx.x;
+  if (probs[prob].done) return;
+  double v[2] = {0, 0};
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int64_t g = (int64_t)prob * P + i;
+    if (nleaf[g] > 0) { v[0] += acc[g]; v[1] += 1.0; }
+  }
+  block_sum<2>(v, red);
+  if (threadIdx.x == 0) { stats[2 * prob] += v[0]; stats[2 * prob + 1] += v[1]; }
+}
+
+__global__ void k_eps_update(const ProbDev* probs, double* stats, double* eps, int n_problems) {
+  const int prob = blockIdx.x * blockDim.x + threadIdx.x;
+  if (prob >= n_problems) return;
+  if (!probs[prob].done && stats[2 * prob + 1] > 0.0) {
+    double e = eps[prob] * exp(stats[2 * prob] / stats[2 * prob + 1] - 0.8);
+    e = e < 1e-4 ? 1e-4 : (e > 2.0 ? 2.0 : e);
+    eps[prob] = e;
+  }
+  stats[2 * prob] = 0.0;
+  stats[2 * prob + 1] = 0.0;
+}
+
+__global__ void k_set_int(int32_t* p, int v) { *p = v; }
+
+__global__ void k_to_f32(const double* a, float* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void k_philox(const uint64_t* ctr, uint64_t k0, uint64_t k1, int64_t n,
+                         uint64_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Rand4 r = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+  for (int j = 0; j < 4; ++j) out[4 * i + j] = r.w[j];
+}
+
+}  // namespace tsmc

@@ -1,0 +1,654 @@
+// likelihood.cuh -- batched residual, Gaussian log-likelihood and adjoint gradient.
+//
+// One thread block evaluates one particle: its K active components against the
+// N samples of its problem.  Threads own R consecutive samples of a segment of
+// blockDim*R samples; the residual of a segment lives in registers.
+//
+//   forward  r_n = d_n - sum_{k<K} h(t_n; theta_k)                (Sec. 5, time domain)
+//            ll_old/ll_new = -1/2 sum r_n^2/sigma^2 over n<n1 / n>=n1
+//   adjoint  dlogL_c/dtheta_kd = sum_n c_n r_n dh_k/dtheta_d / sigma^2, c_n = 1 or beta
+//            (tempered bridges, Eqs. prior_bridge and reuse_bridge)
+//
+// FP64 path: every template value computed directly per sample in the order
+// the definition states (phase ((2pi f) t + (pi fdot)(t t)) + phi0).
+// Mixed path: FP32 templates and residuals.  Pulses use an exact FP32 anchor
+// v0 = (t - t0) sqrt(log2 e / 2)/w per 8 samples (double-float product of the
+// sample index) and the multiplicative recurrence g_{j+1} = g_j q_j,
+// q_{j+1} = q_j rho (rho = 2^(-2 delta^2)); sinusoids use a double-float phase
+// anchor per thread, reduced mod 2pi with a three-part Cody-Waite split of 2pi,
+// then a rotation recurrence.  Partial sums are FP32 over <= 32 samples and a
+// 5-level warp tree, FP64 above (blocked pairwise summation).
+#pragma once
+#include "common.cuh"
+
+namespace tsmc {
+
+// ---------------------------------------------------------------------------
+// coordinate map (logit -> prior range) and log prior density of z
+// ---------------------------------------------------------------------------
+struct PriorArgs {
+  int model;
+  double amp_mean, amp_sd;
+};
+
+__device__ __forceinline__ void coord(const ProbDev& pb, const PriorArgs& pa, int d, double z,
+                                      double& th, double& dth, double& lp, double& pg,
+                                      double& pc) {
+  if (pa.model == PULSE_LINAMP) {
+    const double sd = pa.amp_sd, dz = (z - pa.amp_mean) / sd;
+    th = z; dth = 1.0;
+    lp = -0.5 * dz * dz - log(sd) - 0.5 * log(kTwoPi);
+    pg = -(z - pa.amp_mean) / (sd * sd);
+    pc = 1.0 / (sd * sd);
+    return;
+  }
+  const double s = logistic(z);
+  const double ds = __dmul_rn(s, __dadd_rn(1.0, -s));
+  if (pb.logmask & (1u << d)) {
+    const double span = __dadd_rn(pb.lhi[d], -pb.llo[d]);
+    th = exp(__dadd_rn(pb.llo[d], __dmul_rn(span, s)));
+    dth = __dmul_rn(__dmul_rn(th, span), ds);
+  } else {
+    const double span = __dadd_rn(pb.hi[d], -pb.lo[d]);
+    th = __dadd_rn(pb.lo[d], __dmul_rn(span, s));
+    dth = __dmul_rn(span, ds);
+  }
+  const double a = fabs(z);
+  lp = -a - 2.0 * log1p(exp(-a));
+  pg = 1.0 - 2.0 * s;
+  pc = 2.0 * s * (1.0 - s);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 helpers (hand-written PTX for the SFU approximations)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2a(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sina(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cosa(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// a + m * delta with a = a_hi + a_lo, delta = d_hi + d_lo (double-float); the product
+// m * d_hi is split exactly with an FMA, so the result carries the error of one FP32
+// rounding of the final value only.
+__device__ __forceinline__ float dd_axpy(float a_hi, float a_lo, float d_hi, float d_lo, float m) {
+  const float p = __fmul_rn(m, d_hi);
+  const float e = __fmaf_rn(m, d_hi, -p);
+  const float s = __fadd_rn(a_hi, p);
+  const float lo = __fmaf_rn(m, d_lo, a_lo);
+  return __fadd_rn(s, __fadd_rn(e, lo));
+}
+
+// 2pi = C1 + C2 + C3 (each the FP32 rounding of the remainder)
+constexpr float kC1 = 6.2831854820251465f;
+constexpr float kC2 = -1.7484555314695172e-07f;
+constexpr float kC3 = -6.8604980400235275e-15f;
+constexpr float kInv2Pi = 0.15915493667125702f;
+
+// ---------------------------------------------------------------------------
+// Per-component FP32 constants of the mixed path (NCF floats per component)
+// ---------------------------------------------------------------------------
+constexpr int NCF = 12;
+constexpr double kLog2E = 1.4426950408889634074;
+constexpr double kCu = 1.1774100225154746910;   // sqrt(2 ln 2): u = v * kCu
+
+// pulse: v = (t - t0) kappa, kappa = sqrt(log2(e)/2)/w, g = 2^(-v^2)
+__device__ __forceinline__ void pulse_prep(double A, double t0, double w, const ProbDev& pb,
+                                           float* cf) {
+  const double kap = sqrt(0.5 * kLog2E) / w;
+  const double a0 = (pb.t_origin - t0) * kap;
+  const double del = pb.dt * kap;
+  const float a_hi = (float)a0, d_hi = (float)del;
+  cf[0] = (float)A;
+  cf[1] = a_hi;
+  cf[2] = (float)(a0 - (double)a_hi);
+  cf[3] = d_hi;
+  cf[4] = (float)(del - (double)d_hi);
+  cf[5] = (float)exp2(-2.0 * del * del);
+  cf[6] = (float)(2.0 * del);
+  cf[7] = (float)(del * del);
+  cf[8] = del > 0.5 ? 1.0f : 0.0f;   // coarse grid: evaluate every sample directly
+}
+
+// sinusoid: phi(n) = phi_o + Om n + Gam n^2 with phi_o the phase at t_origin,
+// Om = 2pi (f + fdot t_origin) dt, Gam = pi fdot dt^2
+__device__ __forceinline__ void sin_prep(double A, double f, double fd, double p0,
+                                         const ProbDev& pb, float* cf) {
+  const double to = pb.t_origin;
+  double phi = ((kTwoPi * f) * to + (kPi * fd) * (to * to)) + p0;
+  phi = remainder(phi, kTwoPi);
+  const double om = (kTwoPi * f + kTwoPi * fd * to) * pb.dt;
+  const float om_hi = (float)om;
+  cf[0] = (float)A;
+  cf[1] = (float)phi;
+  cf[2] = om_hi;
+  cf[3] = (float)(om - (double)om_hi);
+  cf[4] = (float)(kPi * fd * pb.dt * pb.dt);
+  double so, co;
+  sincos(om, &so, &co);
+  cf[5] = (float)co;
+  cf[6] = (float)so;
+}
+
+__device__ __forceinline__ void sin_anchor(const float* cf, float m, float& c, float& s) {
+  const float p = __fmul_rn(m, cf[2]);
+  const float e = __fmaf_rn(m, cf[2], -p);
+  const float kq = rintf(__fmul_rn(p, kInv2Pi));
+  float r = __fmaf_rn(-kq, kC1, p);
+  r = __fmaf_rn(-kq, kC2, r);
+  r = __fmaf_rn(-kq, kC3, r);
+  const float extra = __fadd_rn(e, __fmaf_rn(m, cf[3], __fmul_rn(cf[4], __fmul_rn(m, m))));
+  r = __fadd_rn(__fadd_rn(r, extra), cf[1]);
+  const float k2 = rintf(__fmul_rn(r, kInv2Pi));
+  r = __fmaf_rn(-k2, kC1, r);
+  r = __fmaf_rn(-k2, kC2, r);
+  c = cosa(r);
+  s = sina(r);
+}
+
+// template values of one component on the thread's R samples starting at index m
+template <int MODEL, int R>
+__device__ __forceinline__ void mixed_vals(const float* cf, float m, float (&h)[R]) {
+  if (MODEL == SINUSOID) {
+    float c, s;
+    sin_anchor(cf, m, c, s);
+    const float A = cf[0], rc = cf[5], rs = cf[6];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      h[j] = A * c;
+      const float c2 = __fmaf_rn(c, rc, -s * rs);
+      s = __fmaf_rn(s, rc, c * rs);
+      c = c2;
+    }
+  } else {
+    const float A = cf[0];
+    const float v00 = dd_axpy(cf[1], cf[2], cf[3], cf[4], m);
+    if (cf[8] != 0.0f) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const float v = __fmaf_rn((float)j, cf[3], v00);
+        h[j] = A * ex2a(-v * v);
+      }
+    } else {
+#pragma unroll
+      for (int c8 = 0; c8 < R / 8; ++c8) {
+        const float v0 = __fmaf_rn((float)(8 * c8), cf[3], v00);
+        float g = ex2a(-v0 * v0);
+        float q = ex2a(fminf(-__fmaf_rn(v0, cf[6], cf[7]), 64.0f));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          h[8 * c8 + j] = A * g;
+          g *= q;
+          q *= cf[5];
+        }
+      }
+    }
+  }
+}
+
+// adjoint partial sums of one component over the thread's samples (rc = c_n r_n / sigma^2)
+//   pulse:    s0 = sum rc g, s1 = sum rc g v, s2 = sum rc g v^2
+//   sinusoid: s0 = sum rc cos, s1 = sum rc sin, s2 = sum rc sin n, s3 = sum rc sin n^2
+template <int MODEL, int R>
+__device__ __forceinline__ void mixed_adj(const float* cf, float m, const float (&rc)[R],
+                                          float (&o)[4]) {
+  if (MODEL == SINUSOID) {
+    float c, s;
+    sin_anchor(cf, m, c, s);
+    const float rcs = cf[5], rsn = cf[6];
+    float sc = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      sc = __fmaf_rn(rc[j], c, sc);
+      const float p = rc[j] * s;
+      u0 += p;
+      u1 = __fmaf_rn(p, (float)j, u1);
+      u2 = __fmaf_rn(p, (float)(j * j), u2);
+      const float c2 = __fmaf_rn(c, rcs, -s * rsn);
+      s = __fmaf_rn(s, rcs, c * rsn);
+      c = c2;
+    }
+    o[0] = sc;
+    o[1] = u0;
+    o[2] = __fmaf_rn(m, u0, u1);
+    o[3] = __fmaf_rn(m, __fmaf_rn(m, u0, 2.0f * u1), u2);
+  } else {
+    const float v00 = dd_axpy(cf[1], cf[2], cf[3], cf[4], m);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    if (cf[8] != 0.0f) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const float v = __fmaf_rn((float)j, cf[3], v00);
+        const float p = rc[j] * ex2a(-v * v);
+        s0 += p;
+        s1 = __fmaf_rn(p, v, s1);
+        s2 = __fmaf_rn(p * v, v, s2);
+      }
+    } else {
+      const float del = cf[3], del2 = cf[7], rho = cf[5];
+#pragma unroll
+      for (int c8 = 0; c8 < R / 8; ++c8) {
+        const float v0 = __fmaf_rn((float)(8 * c8), del, v00);
+        float g = ex2a(-v0 * v0);
+        float q = ex2a(fminf(-__fmaf_rn(v0, cf[6], del2), 64.0f));
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float p = rc[8 * c8 + j] * g;
+          a0 += p;
+          a1 = __fmaf_rn(p, (float)j, a1);
+          a2 = __fmaf_rn(p, (float)(j * j), a2);
+          g *= q;
+          q *= rho;
+        }
+        // sum p v = v0 a0 + del a1;  sum p v^2 = v0^2 a0 + 2 v0 del a1 + del^2 a2
+        s0 += a0;
+        s1 += __fmaf_rn(v0, a0, del * a1);
+        s2 += __fmaf_rn(v0, __fmaf_rn(v0, a0, 2.0f * del * a1), del2 * a2);
+      }
+    }
+    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = 0.f;
+  }
+}
+
+// Gauss-Newton partial sums (metric only): cw = c_n / sigma^2 (0 for padding)
+//   pulse: (sum cw g^2, sum cw g^2 v^2, sum cw g^2 v^4); sinusoid: (sum cw cos^2,
+//   sum cw sin^2 t^2, sum cw sin^2 t^4, sum cw sin^2) with t in FP32
+template <int MODEL, int R>
+__device__ __forceinline__ void mixed_fis(const float* cf, float m, const float (&cw)[R],
+                                          float t_o, float dt, float (&o)[4]) {
+  o[0] = o[1] = o[2] = o[3] = 0.f;
+  if (MODEL == SINUSOID) {
+    float c, s;
+    sin_anchor(cf, m, c, s);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float t = __fmaf_rn(m + (float)j, dt, t_o);
+      const float s2 = cw[j] * s * s, t2 = t * t;
+      o[0] = __fmaf_rn(cw[j] * c, c, o[0]);
+      o[1] = __fmaf_rn(s2, t2, o[1]);
+      o[2] = __fmaf_rn(s2 * t2, t2, o[2]);
+      o[3] += s2;
+      const float c2 = __fmaf_rn(c, cf[5], -s * cf[6]);
+      s = __fmaf_rn(s, cf[5], c * cf[6]);
+      c = c2;
+    }
+  } else {
+    const float v00 = dd_axpy(cf[1], cf[2], cf[3], cf[4], m);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float v = __fmaf_rn((float)j, cf[3], v00);
+      const float g = ex2a(-v * v);
+      const float a = cw[j] * g * g, v2 = v * v;
+      o[0] += a;
+      o[1] = __fmaf_rn(a, v2, o[1]);
+      o[2] = __fmaf_rn(a * v2, v2, o[2]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 templates (direct, in the defining order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double time_of(const ProbDev& pb, int64_t n) {
+  return __dadd_rn(pb.t_origin, __dmul_rn((double)n, pb.dt));
+}
+
+template <int MODEL>
+__device__ __forceinline__ double fp64_val(const double* th, double tw0, double tw1, double t,
+                                           double* dh) {
+  if (MODEL == SINUSOID) {
+    const double A = th[0], f = th[1], fd = th[2], p0 = th[3];
+    const double phi = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(kTwoPi, f), t),
+                                           __dmul_rn(__dmul_rn(kPi, fd), __dmul_rn(t, t))),
+                                 p0);
+    double sph, cph;
+    sincos(phi, &sph, &cph);
+    if (dh) {
+      const double mas = __dmul_rn(-A, sph);
+      dh[0] = cph;
+      dh[1] = __dmul_rn(mas, __dmul_rn(kTwoPi, t));
+      dh[2] = __dmul_rn(mas, __dmul_rn(kPi, __dmul_rn(t, t)));
+      dh[3] = mas;
+    }
+    return __dmul_rn(A, cph);
+  } else {
+    const double A = th[0];
+    const double t0 = MODEL == PULSE ? th[1] : tw0;
+    const double w = MODEL == PULSE ? th[2] : tw1;
+    const double u = __ddiv_rn(__dadd_rn(t, -t0), w);
+    const double g = exp(__dmul_rn(__dmul_rn(-0.5, u), u));
+    if (dh) {
+      dh[0] = g;
+      if (MODEL == PULSE) {
+        const double ag = __dmul_rn(A, g);
+        dh[1] = __ddiv_rn(__dmul_rn(ag, u), w);
+        dh[2] = __ddiv_rn(__dmul_rn(__dmul_rn(ag, u), u), w);
+      }
+    }
+    return __dmul_rn(A, g);
+  }
+}
+
+template <int MODEL>
+__host__ __device__ constexpr int model_d() { return MODEL == SINUSOID ? 4 : (MODEL == PULSE ? 3 : 1); }
+
+// ---------------------------------------------------------------------------
+// Shared-memory scratch of one block evaluation
+// ---------------------------------------------------------------------------
+struct EvalSmem {
+  double* th;     // [KDmax] theta
+  double* dth;    // [KDmax] dtheta/dz
+  double* pg;     // [KDmax] prior gradient
+  double* pc;     // [KDmax] prior curvature
+  float* cf;      // [kmax][NCF] mixed-path constants
+  double* wacc;   // [nwarps][KDmax] per-warp gradient slot sums
+  double* wfis;   // [nwarps][KDmax] per-warp Gauss-Newton slot sums
+  double* red;    // [32*4] reduction scratch
+  double* scal;   // [4]: logp, ll_old, ll_new, log prior
+  const double* tw;  // LINAMP fixed (t0, w) [kmax][2] (global)
+};
+
+template <int MODEL>
+__device__ __forceinline__ void finish_component(int prec, const double* th, const double* S,
+                                                 const ProbDev& pb, double* g) {
+  // S: slot sums (already scaled by 1/sigma^2 and c_n); g: dlogL/dtheta
+  if (prec == FP64) {
+    for (int d = 0; d < model_d<MODEL>(); ++d) g[d] = S[d];
+    return;
+  }
+  if (MODEL == SINUSOID) {
+    const double A = th[0], to = pb.t_origin, dt = pb.dt;
+    g[0] = S[0];
+    g[1] = -A * kTwoPi * (to * S[1] + dt * S[2]);
+    g[2] = -A * kPi * (to * to * S[1] + 2.0 * to * dt * S[2] + dt * dt * S[3]);
+    g[3] = -A * S[1];
+  } else if (MODEL == PULSE) {
+    const double aw = th[0] / th[2];
+    g[0] = S[0];
+    g[1] = aw * kCu * S[1];
+    g[2] = aw * kCu * kCu * S[2];
+  } else {
+    g[0] = S[0];
+  }
+}
+
+template <int MODEL>
+__device__ __forceinline__ void finish_fisher(int prec, const double* th, const double* F,
+                                              double* f) {
+  if (prec == FP64) {
+    for (int d = 0; d < model_d<MODEL>(); ++d) f[d] = F[d];
+    return;
+  }
+  if (MODEL == SINUSOID) {
+    const double A2 = th[0] * th[0];
+    f[0] = F[0];
+    f[1] = A2 * kTwoPi * kTwoPi * F[1];
+    f[2] = A2 * kPi * kPi * F[2];
+    f[3] = A2 * F[3];
+  } else if (MODEL == PULSE) {
+    const double aw = th[0] / th[2];
+    f[0] = F[0];
+    f[1] = aw * aw * kCu * kCu * F[1];
+    f[2] = aw * aw * kCu * kCu * kCu * kCu * F[2];
+  } else {
+    f[0] = F[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-component setup: theta, Jacobians, prior terms and path constants.
+// Must be called by all threads; ends with __syncthreads.  Returns the thread's
+// share of the log prior (summed by the caller's block reduction).
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC>
+__device__ double eval_setup(const ProbDev& pb, const PriorArgs& pa, int K, const double* z,
+                             EvalSmem& sm) {
+  constexpr int D = model_d<MODEL>();
+  double lp_sum = 0.0;
+  for (int i = threadIdx.x; i < K * D; i += blockDim.x) {
+    double th, dth, lp, pg, pc;
+    coord(pb, pa, i % D, z[i], th, dth, lp, pg, pc);
+    sm.th[i] = th; sm.dth[i] = dth; sm.pg[i] = pg; sm.pc[i] = pc;
+    lp_sum += lp;
+  }
+  __syncthreads();
+  if (PREC == MIXED) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const double* t = sm.th + k * D;
+      float* cf = sm.cf + k * NCF;
+      if (MODEL == SINUSOID) sin_prep(t[0], t[1], t[2], t[3], pb, cf);
+      else if (MODEL == PULSE) pulse_prep(t[0], t[1], t[2], pb, cf);
+      else pulse_prep(t[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
+    }
+    __syncthreads();
+  }
+  return lp_sum;
+}
+
+// ---------------------------------------------------------------------------
+// Block evaluation of one particle.  All threads call it.  Writes
+//   sm.scal[0..2] = logp, ll_old, ll_new   (visible to all threads on return)
+//   grad_out[K*D] = dlogp/dz  (if GRAD; may alias shared memory)
+//   fis_out[K*D]  = Gauss-Newton diagonal + prior curvature per element (if FISHER)
+// R: samples per thread per segment (multiple of 8).
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
+__device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
+                           const double* z, EvalSmem& sm, double* grad_out, double* fis_out) {
+  constexpr int D = model_d<MODEL>();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  const double lp_sum = eval_setup<MODEL, PREC>(pb, pa, K, z, sm);
+
+  const int64_t N = pb.n, n1 = pb.n1;
+  const float beta_f = (float)beta, inv_s2_f = (float)pb.inv_s2;
+  double acc_old = 0.0, acc_new = 0.0;
+  double ga[2][4], fa[2][4];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { ga[s][d] = 0.0; fa[s][d] = 0.0; }
+
+  const int64_t seg = (int64_t)blockDim.x * R;
+  for (int64_t base = 0; base < N; base += seg) {
+    const int64_t wfirst = base + (int64_t)warp * 32 * R;
+    if (wfirst >= N) continue;  // whole warp past the end (warp-uniform)
+    const int64_t m = base + (int64_t)tid * R;
+
+    if (PREC == MIXED) {
+      float r[R];
+      if (m + R <= N) {
+        const float4* src = reinterpret_cast<const float4*>(pb.d32 + m);
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+          const float4 v = src[q];
+          r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
+      }
+      const float mf = (float)m;
+      for (int k = 0; k < K; ++k) {
+        float h[R];
+        mixed_vals<MODEL, R>(sm.cf + k * NCF, mf, h);
+#pragma unroll
+        for (int j = 0; j < R; ++j) r[j] -= h[j];
+      }
+      // residual energy and the adjoint weights rc = c_n r_n / sigma^2
+      float so = 0.f, sn = 0.f;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t n = m + j;
+        const bool valid = n < N, old = n < n1;
+        const float rr = valid ? r[j] : 0.0f;
+        const float e = rr * rr;
+        if (old) so += e; else sn += e;
+        r[j] = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
+      }
+      acc_old += (double)so;
+      acc_new += (double)sn;
+      if (GRAD) {
+        for (int k = 0; k < K; ++k) {
+          float o[4];
+          mixed_adj<MODEL, R>(sm.cf + k * NCF, mf, r, o);
+#pragma unroll
+          for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
+          if (lane == (k & 31)) {
+            if (k < 32) {
+#pragma unroll
+              for (int d = 0; d < D; ++d) ga[0][d] += (double)o[d];
+            } else {
+#pragma unroll
+              for (int d = 0; d < D; ++d) ga[1][d] += (double)o[d];
+            }
+          }
+        }
+      }
+      if (FISHER) {
+        float cw[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int64_t n = m + j;
+          cw[j] = n < N ? (n < n1 ? inv_s2_f : beta_f * inv_s2_f) : 0.0f;
+        }
+        for (int k = 0; k < K; ++k) {
+          float o[4];
+          mixed_fis<MODEL, R>(sm.cf + k * NCF, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
+#pragma unroll
+          for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
+          if (lane == (k & 31)) {
+            if (k < 32) {
+#pragma unroll
+              for (int d = 0; d < D; ++d) fa[0][d] += (double)o[d];
+            } else {
+#pragma unroll
+              for (int d = 0; d < D; ++d) fa[1][d] += (double)o[d];
+            }
+          }
+        }
+      }
+    } else {
+      // ---------------- FP64 path ----------------
+      double hs[R], r[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) hs[j] = 0.0;
+      for (int k = 0; k < K; ++k) {
+        const double* th = sm.th + k * D;
+        const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
+        const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), nullptr));
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t n = m + j;
+        const bool valid = n < N, old = n < n1;
+        const double rr = valid ? __dadd_rn(pb.d64[valid ? n : 0], -hs[j]) : 0.0;
+        const double e = __dmul_rn(rr, rr);
+        if (old) acc_old += e; else acc_new += e;
+        r[j] = __dmul_rn(old ? 1.0 : beta, rr);   // c_n r_n (1/sigma^2 applied at the end)
+      }
+      if (GRAD || FISHER) {
+        for (int k = 0; k < K; ++k) {
+          const double* th = sm.th + k * D;
+          const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
+          const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
+          double o[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            double dh[4];
+            fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), dh);
+            const int64_t n = m + j;
+            const double cn = n < N ? (n < n1 ? 1.0 : beta) : 0.0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              o[d] += __dmul_rn(r[j], dh[d]);
+              if (FISHER) f[d] += cn * dh[d] * dh[d];
+            }
+          }
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            if (GRAD) o[d] = warp_sum(o[d]);
+            if (FISHER) f[d] = warp_sum(f[d]);
+          }
+          if (lane == (k & 31)) {
+            const int s = k < 32 ? 0 : 1;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              if (s == 0) { ga[0][d] += o[d]; fa[0][d] += f[d]; }
+              else { ga[1][d] += o[d]; fa[1][d] += f[d]; }
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // ---- gradient / Gauss-Newton assembly: per-warp slots -> shared -> components ----
+  if (GRAD || FISHER) {
+    const int KDm = K * D;
+    for (int k = lane; k < K; k += 32) {
+      const int s = k < 32 ? 0 : 1;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (GRAD) sm.wacc[warp * KDm + k * D + d] = s == 0 ? ga[0][d] : ga[1][d];
+        if (FISHER) sm.wfis[warp * KDm + k * D + d] = s == 0 ? fa[0][d] : fa[1][d];
+      }
+    }
+    // warps that skipped every segment still hold zeros: they wrote them above
+    __syncthreads();
+    const double is2 = PREC == FP64 ? pb.inv_s2 : 1.0;
+    for (int k = tid; k < K; k += blockDim.x) {
+      double S[4] = {0, 0, 0, 0}, F[4] = {0, 0, 0, 0}, g[4], f[4];
+      for (int w = 0; w < nw; ++w) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          if (GRAD) S[d] += sm.wacc[w * KDm + k * D + d];
+          if (FISHER) F[d] += sm.wfis[w * KDm + k * D + d];
+        }
+      }
+      const double* th = sm.th + k * D;
+      if (GRAD) {
+        finish_component<MODEL>(PREC, th, S, pb, g);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int i = k * D + d;
+          grad_out[i] = g[d] * is2 * sm.dth[i] + sm.pg[i];
+        }
+      }
+      if (FISHER) {
+        finish_fisher<MODEL>(PREC, th, F, f);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int i = k * D + d;
+          fis_out[i] = f[d] * is2 * sm.dth[i] * sm.dth[i] + sm.pc[i];
+        }
+      }
+    }
+  }
+  double v[3] = {acc_old, acc_new, lp_sum};
+  block_sum<3>(v, sm.red);
+  if (tid == 0) {
+    const double lo = -0.5 * v[0] * pb.inv_s2, ln = -0.5 * v[1] * pb.inv_s2;
+    sm.scal[0] = lo + beta * ln + v[2];
+    sm.scal[1] = lo;
+    sm.scal[2] = ln;
+    sm.scal[3] = v[2];
+  }
+  __syncthreads();
+}
+
+}  // namespace tsmc

@@ -1,0 +1,336 @@
+"""CUDA path vs the oracle, through the C ABI, on the same seeded inputs.
+
+Sizes span several segments of samples per block and a ragged tail; K ranges
+over 0..kmax.  FP64 path: relative 1e-12; mixed path: relative 1e-5 (gradients
+relative to the sum of absolute terms, i.e. the condition of the sum).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_17674_b300 import capi, sampler, synth
+from gpu_helpers import (TOL, assert_eval_parity, context_with_population, dev_tensor,
+                         population, torch)
+
+pytestmark = pytest.mark.gpu
+
+
+def test_philox_matches_oracle():
+    wl = synth.config1()
+    ctx = sampler.open_context(wl, capi.FP64)
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2**63, size=(64, 4), dtype=np.uint64)
+    out = ctx.philox(ctr.ravel(), 12345, 678)
+    for i in range(64):
+        assert (out[4 * i: 4 * i + 4] == oracle.philox(ctr[i], [12345, 678])).all()
+
+
+CASES = [
+    # model, N, kmax, n1, P
+    ("pulse", 3000, 6, 0, 48),
+    ("pulse", 5000, 5, 1700, 40),
+    ("pulse", 100, 4, 0, 16),
+    ("sinusoid", 9000, 5, 0, 24),
+    ("sinusoid", 6000, 4, 2500, 16),
+]
+
+
+def _wl(model, n, kmax, P, seed=41):
+    if model == "pulse":
+        return synth.pulse_workload("t", n, 3, kmax, P, seed)
+    return synth.sinusoid_workload("t", n, 3, kmax, P, seed)
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+@pytest.mark.parametrize("model,n,kmax,n1,P", CASES)
+def test_eval_parity(prec, model, n, kmax, n1, P):
+    t = torch()
+    wl = _wl(model, n, kmax, P)
+    z, K = population(wl, 5, P)
+    if model == "sinusoid":
+        # half the particles near the injection (small residuals: the hard case)
+        zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+        for i in range(2, P, 2):
+            k = min(K[i], zt.shape[0])
+            K[i] = k
+            z[i, :k] = zt[:k] + 0.01 * np.random.default_rng(i).standard_normal((k, 4))
+    beta = 0.37
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, beta, n_use=n, n1=n1)
+    bt = dev_tensor([beta], t.float64)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, bt, grad=True)
+    t.cuda.synchronize()
+    ora = oracle.Oracle(wl, n=n, n1=n1)
+    res = ora.logl_grad(z, K, beta)
+    assert_eval_parity(ora, res, lo, ln, lp, g, K, TOL[prec], wl.D)
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_linamp_eval_and_fisher(prec):
+    t = torch()
+    wl = synth.linamp_workload(n=2100, k=3, P=8)
+    rng = np.random.default_rng(2)
+    z = rng.normal(1.0, 1.0, (8, 3, 1))
+    K = np.full(8, 3, np.int32)
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.8)
+    bt = dev_tensor([0.8], t.float64)
+    lo, ln, lp, g, fis = ctx.eval(zd, Kd, bt, grad=True, fisher=True)
+    res = oracle.Oracle(wl).logl_grad(z, K, 0.8, want_fisher=True)
+    assert_eval_parity(None, res, lo, ln, lp, g, K, TOL[prec], 1)
+    np.testing.assert_allclose(fis.cpu().numpy()[:, 0], res["fisher"].sum(1)[:, 0],
+                               rtol=1e-10 if prec == capi.FP64 else 1e-4)
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+@pytest.mark.parametrize("model", ["pulse", "sinusoid"])
+def test_fisher_parity(prec, model):
+    t = torch()
+    wl = _wl(model, 4000, 4, 12)
+    z, K = population(wl, 9, 12)
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.5)
+    bt = dev_tensor([0.5], t.float64)
+    _, _, _, _, fis = ctx.eval(zd, Kd, bt, grad=True, fisher=True)
+    res = oracle.Oracle(wl).logl_grad(z, K, 0.5, want_fisher=True)
+    np.testing.assert_allclose(fis.cpu().numpy(), res["fisher"].sum(1),
+                               rtol=1e-10 if prec == capi.FP64 else 1e-4)
+
+
+def test_init_population_matches_oracle():
+    wl = synth.config1()
+    wl.P = 300
+    ctx = sampler.open_context(wl, capi.FP64)
+    ctx.init_population()
+    z, K, lo, ln = ctx.get_population()
+    zo, Ko = oracle.Oracle(wl).init_population(300)
+    assert np.array_equal(K.cpu().numpy(), Ko)
+    np.testing.assert_allclose(z.cpu().numpy(), zo, rtol=1e-15, atol=1e-15)
+    res = oracle.Oracle(wl).logl_grad(zo, Ko, 0.0)
+    np.testing.assert_allclose(ln.cpu().numpy(), res["ll_new"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("n1", [0, 700])
+def test_rj_move_parity_fp64(n1):
+    t = torch()
+    wl = synth.pulse_workload("t", 1500, 3, 6, 200, 77)
+    z, K = population(wl, 13, 200)
+    ora = oracle.Oracle(wl, n=1500, n1=n1)
+    beta = 0.45
+    ctx, zd, Kd = context_with_population(wl, capi.FP64, z, K, beta, n_use=1500, n1=n1)
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo, Ko = z.copy(), K.copy()
+    out_o = ora.rj_move(4, 2, beta, zo, Ko, lo, ln)
+    # the GPU move reads beta from the context (set_population set it)
+    outd = t.zeros(200, dtype=t.int32, device="cuda")
+    ctx.rj_move(4, 2, outd)
+    zg, Kg, log_, lng = ctx.get_population()
+    assert np.array_equal(outd.cpu().numpy(), out_o)
+    assert np.array_equal(Kg.cpu().numpy(), Ko)
+    np.testing.assert_allclose(zg.cpu().numpy(), zo, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(lng.cpu().numpy(), ln, rtol=1e-10)
+    np.testing.assert_allclose(log_.cpu().numpy(), lo, rtol=1e-10, atol=1e-9)
+    assert set(np.unique(out_o)) >= {1, 2, -1} or len(np.unique(out_o)) >= 3
+
+
+def test_rj_move_mixed_agrees():
+    t = torch()
+    wl = synth.config2(P=512, n=16384)
+    z, K = population(wl, 21, 512)
+    ora = oracle.Oracle(wl)
+    ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.01)
+    r = ora.logl_grad(z, K, 0.01, want_scale=False)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo, Ko = z.copy(), K.copy()
+    out_o = ora.rj_move(1, 0, 0.01, zo, Ko, lo, ln)
+    outd = t.zeros(512, dtype=t.int32, device="cuda")
+    ctx.rj_move(1, 0, outd)
+    zg, Kg, _, lng = ctx.get_population()
+    agree = np.mean(outd.cpu().numpy() == out_o)
+    assert agree > 0.99
+    same = outd.cpu().numpy() == out_o
+    np.testing.assert_allclose(lng.cpu().numpy()[same], ln[same], rtol=1e-5)
+
+
+def test_nuts_parity_fp64():
+    t = torch()
+    wl = synth.pulse_workload("t", 512, 3, 4, 64, 88)
+    ora = oracle.Oracle(wl)
+    rng = np.random.default_rng(0)
+    K = rng.integers(1, 5, 64).astype(np.int32)
+    zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+    z = np.zeros((64, 4, 3))
+    for i in range(64):
+        k = min(K[i], 3)
+        K[i] = k
+        z[i, :k] = zt[:k] + 0.05 * rng.standard_normal((k, 3))
+    beta = 0.6
+    minv = ora.metric(z, K, beta)
+    eps = 0.2
+    ctx, zd, Kd = context_with_population(wl, capi.FP64, z, K, beta)
+    ctx.set_kernel_params([eps], minv[None, :])
+    acc = t.zeros(64, dtype=t.float64, device="cuda")
+    nl = t.zeros(64, dtype=t.int32, device="cuda")
+    fl = t.zeros(64, dtype=t.int32, device="cuda")
+    ctx.nuts_move(3, 1, acc, nl, fl)
+    zg, Kg, lo_g, ln_g = ctx.get_population()
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo = z.copy()
+    acc_o, nl_o, fl_o = ora.nuts_move(3, 1, beta, eps, minv, zo, K, lo, ln)
+    assert np.array_equal(nl.cpu().numpy(), nl_o)
+    assert np.array_equal(fl.cpu().numpy(), fl_o)
+    np.testing.assert_allclose(zg.cpu().numpy(), zo, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(acc.cpu().numpy(), acc_o, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(ln_g.cpu().numpy(), ln, rtol=1e-10)
+    assert np.mean(nl_o) > 3  # the trees were non-trivial
+
+
+def test_nuts_mixed_moves_and_stays_finite():
+    t = torch()
+    wl = synth.config2(P=256, n=16384)
+    z, K = population(wl, 2, 256)
+    ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.001)
+    ctx.update_metric()
+    acc = t.zeros(256, dtype=t.float64, device="cuda")
+    nl = t.zeros(256, dtype=t.int32, device="cuda")
+    ctx.nuts_move(0, 0, acc, nl, None)
+    zg, Kg, _, ln = ctx.get_population()
+    assert np.all(np.isfinite(zg.cpu().numpy()))
+    assert np.all(np.isfinite(ln.cpu().numpy()))
+    moved = nl.cpu().numpy() > 0
+    assert np.all(moved == (K > 0))
+    # carried likelihoods belong to the returned points (mixed path, same kernel)
+    _, ln2, _, _, _ = ctx.eval(zg, Kg, dev_tensor([0.001], t.float64))
+    np.testing.assert_allclose(ln.cpu().numpy(), ln2.cpu().numpy(), rtol=1e-12)
+
+
+def test_temper_and_resample_parity():
+    wl = synth.config1()
+    wl.P = 512
+    ctx = sampler.open_context(wl, capi.FP64)
+    ctx.init_population()
+    _, _, _, ln = ctx.get_population()
+    ell = ln.cpu().numpy()
+    b, lz, e = ctx.temper_reweight_resample(5)
+    bo, inco, esso, logw = oracle.temper(ell, wl.alpha, 0.0)
+    assert b[0] == pytest.approx(bo, abs=1e-13)
+    assert lz[0] == pytest.approx(inco, rel=1e-12, abs=1e-12)
+    assert e[0] == pytest.approx(esso, rel=1e-9)
+    anc = ctx.get_ancestors().cpu().numpy()
+    anc_o = oracle.Oracle(wl).resample(5, logw)
+    assert np.mean(anc == anc_o) > 0.998
+    assert np.all(np.diff(anc) >= 0)
+
+
+def test_metric_parity():
+    wl = synth.pulse_workload("t", 2048, 3, 5, 64, 5)
+    z, K = population(wl, 8, 64)
+    ctx, zd, Kd = context_with_population(wl, capi.FP64, z, K, 0.3)
+    ctx.update_metric()
+    _, m = ctx.get_kernel_params()
+    mo = oracle.Oracle(wl).metric(z, K, 0.3)
+    np.testing.assert_allclose(m[0], mo, rtol=1e-10)
+
+
+def test_stage_graph_matches_eager():
+    res = []
+    for graph in (False, True):
+        wl = synth.config1()
+        wl.P = 256
+        ctx = sampler.open_context(wl, capi.FP64)
+        ctx.init_population()
+        out = [ctx.run_stage(s, use_graph=graph) for s in range(3)]
+        z, K, _, ln = ctx.get_population()
+        res.append((out, z.cpu().numpy(), K.cpu().numpy()))
+    (o1, z1, k1), (o2, z2, k2) = res
+    assert np.array_equal(k1, k2)
+    np.testing.assert_array_equal(z1, z2)
+    for a, b in zip(o1, o2):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_smc_stage_matches_oracle_fp64():
+    """One full stage (temper, resample, metric, RJ + NUTS rounds) on both sides."""
+    wl = synth.config1()
+    wl.P = 128
+    wl.n_mut = 2
+    ctx = sampler.open_context(wl, capi.FP64)
+    ctx.init_population()
+    b, lz, _ = ctx.run_stage(0, use_graph=False)
+    z, K, _, ln = ctx.get_population()
+    ora = oracle.Oracle(wl)
+    res = ora.smc_run(128, max_stages=1)
+    assert b[0] == pytest.approx(res["beta"][0], abs=1e-13)
+    assert lz[0] == pytest.approx(res["logz"], rel=1e-11, abs=1e-11)
+    Kg = K.cpu().numpy()
+    assert np.mean(Kg == res["K"]) > 0.97
+    same = Kg == res["K"]
+    zg = z.cpu().numpy()
+    close = np.all(np.isclose(zg, res["z"], rtol=1e-8, atol=1e-8), axis=(1, 2))
+    assert np.mean(close[same]) > 0.95
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_full_size_pulse_sampled(prec):
+    """N=16384, K_max=40, P=8192 in the benchmark launch configuration; oracle on a sample."""
+    t = torch()
+    wl = synth.config2()
+    z, K = population(wl, 1, wl.P)
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.25)
+    bt = dev_tensor([0.25], t.float64)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, bt, grad=True)
+    t.cuda.synchronize()
+    idx = np.r_[0, 1, np.random.default_rng(0).choice(wl.P, 14, replace=False)]
+    res = oracle.Oracle(wl).logl_grad(z[idx], K[idx], 0.25)
+    assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[prec], 3)
+
+
+@pytest.mark.parametrize("prec", [capi.MIXED])
+def test_full_size_sinusoid_sampled(prec):
+    """N=2^18 Galactic-binary band, K_max=30, P=4096; oracle on a sample of particles."""
+    t = torch()
+    wl = synth.config3()
+    z, K = population(wl, 1, wl.P)
+    zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+    for i in range(2, 40, 2):
+        K[i] = 10
+        z[i, :10] = zt + 1e-4 * np.random.default_rng(i).standard_normal((10, 4))
+        z[i, 10:] = 0.0
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.9)
+    bt = dev_tensor([0.9], t.float64)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, bt, grad=True)
+    t.cuda.synchronize()
+    idx = np.array([0, 1, 2, 3, 4, 8, 9])
+    res = oracle.Oracle(wl).logl_grad(z[idx], K[idx], 0.9)
+    assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[prec], 4)
+
+
+def test_autograd_function_backward():
+    t = torch()
+    wl = synth.pulse_workload("t", 2048, 3, 4, 8, 3)
+    z, K = population(wl, 3, 8)
+    ctx, zd, Kd = context_with_population(wl, capi.FP64, z, K, 1.0)
+    zr = zd.clone().requires_grad_(True)
+    logp = sampler.LoglGrad.apply(ctx, zr, Kd)
+    w = t.arange(8, dtype=t.float64, device="cuda")
+    (logp * w).sum().backward()
+    res = oracle.Oracle(wl).logl_grad(z, K, 1.0)
+    np.testing.assert_allclose(zr.grad.cpu().numpy(), res["grad"] * np.arange(8)[:, None, None],
+                               rtol=1e-10, atol=1e-10)
+
+
+def test_bad_arguments_rejected():
+    wl = synth.config1()
+    ctx = sampler.open_context(wl, capi.FP64)
+    with pytest.raises(capi.TsmcError):
+        ctx.set_problem(0, np.array([1.0, np.nan]), 0.0, 1.0, 0.1, synth.PULSE_LO, synth.PULSE_HI, 4)
+    with pytest.raises(capi.TsmcError):
+        ctx.set_problem(3, np.ones(8), 0.0, 1.0, 0.1, synth.PULSE_LO, synth.PULSE_HI, 4)
+    with pytest.raises(capi.TsmcError):
+        ctx.nuts_move(-1, 0)
+    t = torch()
+    with pytest.raises(capi.TsmcError):
+        ctx.set_population(dev_tensor(np.zeros((512, 10, 3))),
+                           dev_tensor(np.full(512, 11, np.int32)))
