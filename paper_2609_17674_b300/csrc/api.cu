@@ -95,7 +95,7 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->max_depth < 1 || cfg->max_depth > kMaxDepth || cfg->n_mut < 0) return TSMC_EINVAL;
   if (!(cfg->alpha > 0.0 && cfg->alpha <= 1.0)) return TSMC_EINVAL;
   if (cfg->schedule == TSMC_SCHED_ROUNDS && !(cfg->p_birth > 0.0 && cfg->p_death > 0.0)) return TSMC_EINVAL;
-  if (cfg->threads != 0 && (cfg->threads < 32 || cfg->threads > 512 || cfg->threads % 32)) return TSMC_EINVAL;
+  if (cfg->threads != 0 && (cfg->threads < 32 || cfg->threads > 256 || cfg->threads % 32)) return TSMC_EINVAL;
   if (cfg->samples_per_thread != 0 && cfg->samples_per_thread != 16 && cfg->samples_per_thread != 32) return TSMC_EINVAL;
   return TSMC_OK;
 }
@@ -436,7 +436,7 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->D = model_dim(cfg->model);
   c->kd = cfg->kmax * c->D;
   c->Ptot = (int64_t)cfg->n_problems * cfg->particles;
-  c->T = cfg->threads ? cfg->threads : (cfg->precision == TSMC_MIXED ? 256 : 128);
+  c->T = cfg->threads ? cfg->threads : 128;   // best measured for both paths (N = 16384)
   c->R = cfg->samples_per_thread ? cfg->samples_per_thread : 32;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   Layout L;

@@ -59,6 +59,7 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
   if (sp.fisher) { sm.wfis = d; d += (size_t)sp.nw * sp.kd; } else { sm.wfis = nullptr; }
   sm.red = d; d += 128;
   sm.scal = d; d += 4;
+  if (reinterpret_cast<uintptr_t>(d) & 8) d += 1;   // float4 loads of the constants
   sm.cf = reinterpret_cast<float*>(d);
   p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kd * NCF);
   // keep 8-byte alignment for what follows
@@ -75,8 +76,12 @@ struct EvalIO {
   double* ll_old; double* ll_new; double* logp; double* grad; double* fis_sum;
 };
 
+// particle-block kernels: at most 256 threads; the register budget leaves room for 2
+// (32 samples per thread) or 3 (16 samples per thread) resident blocks per SM
+#define TSMC_PARTICLE_BOUNDS __launch_bounds__(256, (PREC == MIXED && R == 16) ? 3 : 2)
+
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
-__global__ void __launch_bounds__(512) k_eval(KParams kp, EvalIO io, SmemPlan sp) {
+__global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   const int64_t gi = blockIdx.x;
@@ -144,7 +149,7 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
 // Reversible-jump birth/death: one block per particle (Sec. 3.1 nested map).
 // ---------------------------------------------------------------------------
 template <int MODEL, int PREC, int R>
-__global__ void __launch_bounds__(512) k_rj(KParams kp, int round, int32_t* outcome, SmemPlan sp) {
+__global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcome, SmemPlan sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   __shared__ int s_move;       // 0 none, 1 birth, 2 death
@@ -308,10 +313,10 @@ __device__ __forceinline__ double warp_dot_minv(const double* a, const double* b
 }
 
 template <int MODEL, int PREC, int R>
-__global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
+__global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
-  __shared__ int s_flag[4];          // 0: subtree valid, 1: stop, 2: direction
+  __shared__ int s_flag[8];
   __shared__ double s_ctl[8];
   const int64_t gi = blockIdx.x;
   const int prob = (int)(gi / kp.P);
@@ -352,14 +357,11 @@ __global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
   block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
-  // control state (meaningful in warp 0)
-  double H0 = 0, logW = 0, sum_acc = 0, cand_lo = 0, cand_ln = 0, sub_logW = 0, sub_lo = 0,
-         sub_ln = 0;
-  int leaves = 0, diverged = 0, depth_done = 0;
+  // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
+  // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
+  // s_ctl: 0 H0, 1 logW, 2 sum_acc, 3 cand_lo, 4 cand_ln, 5 sub_logW, 6 sub_lo, 7 sub_ln
+  // s_flag: 0 subtree valid, 1 stop, 2 direction, 3 leaves, 4 diverged, 5 depth done
   if (warp == 0) {
-    const double logp0 = sm.scal[0];
-    cand_lo = sm.scal[1];
-    cand_ln = sm.scal[2];
     for (int i = lane; i < n; i += 32) {
       const double pm = sqrt(1.0 / minv[i % D]) *
                         draw_normal(kp.seed, prob, li, stage, round, PU_MOMENTUM, (uint64_t)i);
@@ -371,8 +373,15 @@ __global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out
     double kin = 0.0;
     for (int i = lane; i < n; i += 32) kin += minv[i % D] * pL[i] * pL[i];
     kin = warp_sum(kin);
-    H0 = -logp0 + 0.5 * kin;
-    logW = -H0;
+    if (lane == 0) {
+      const double H0 = -sm.scal[0] + 0.5 * kin;
+      s_ctl[0] = H0;
+      s_ctl[1] = -H0;
+      s_ctl[2] = 0.0;
+      s_ctl[3] = sm.scal[1];
+      s_ctl[4] = sm.scal[2];
+      s_flag[3] = 0; s_flag[4] = 0; s_flag[5] = 0;
+    }
   }
   for (int depth = 0; depth < kp.max_depth; ++depth) {
     const int nsub = 1 << depth;
@@ -381,14 +390,15 @@ __global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out
       if (lane == 0) {
         const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_DIRECTION, (uint64_t)depth);
         dir = u01(w.w[0]) < 0.5 ? -1 : 1;
+        s_ctl[5] = -INFINITY;
+        s_flag[0] = 1;
+        s_flag[2] = dir;
       }
       dir = __shfl_sync(0xffffffffu, dir, 0);
       const double *zs0 = dir > 0 ? zR : zL, *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
       for (int i = lane; i < n; i += 32) {
         z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0.0;
       }
-      sub_logW = -INFINITY;
-      if (lane == 0) { s_flag[0] = 1; s_flag[2] = dir; }
     }
     __syncthreads();
     const double de = s_flag[2] * eps;
@@ -412,31 +422,32 @@ __global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out
         }
         kin = warp_sum(kin);
         const double H = -sm.scal[0] + 0.5 * kin;
-        const int leaf_id = (nsub - 1) + l;
-        ++leaves;
-        if (isfinite(H)) { const double a = exp(H0 - H); sum_acc += a < 1.0 ? a : 1.0; }
-        int ok = 1;
-        if (!isfinite(H) || H - H0 > 1000.0) {
-          ok = 0;
-          diverged = 1;
-        } else {
-          const double lw = -H;
-          const double nl = logaddexp(sub_logW, lw);
-          int take = (l == 0);
-          if (!take) {
-            int t = 0;
-            if (lane == 0) {
+        const double H0 = s_ctl[0];
+        int ok = 1, take = 0;
+        if (lane == 0) {
+          s_flag[3] += 1;
+          if (isfinite(H)) { const double a = exp(H0 - H); s_ctl[2] += a < 1.0 ? a : 1.0; }
+          if (!isfinite(H) || H - H0 > 1000.0) {
+            ok = 0;
+            s_flag[4] = 1;
+          } else {
+            const double lw = -H;
+            const double nl = logaddexp(s_ctl[5], lw);
+            take = (l == 0);
+            if (!take) {
+              const int leaf_id = (nsub - 1) + l;
               const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_LEAF, (uint64_t)leaf_id);
-              t = u01(w.w[0]) < exp(lw - nl);
+              take = u01(w.w[0]) < exp(lw - nl);
             }
-            take = __shfl_sync(0xffffffffu, t, 0);
+            if (take) { s_ctl[6] = sm.scal[1]; s_ctl[7] = sm.scal[2]; }
+            s_ctl[5] = nl;
           }
-          if (take) {
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        take = __shfl_sync(0xffffffffu, take, 0);
+        if (ok) {
+          if (take)
             for (int i = lane; i < n; i += 32) sz[i] = z1[i];
-            sub_lo = sm.scal[1];
-            sub_ln = sm.scal[2];
-          }
-          sub_logW = nl;
           for (int mm = 1; mm <= depth; ++mm) {
             if ((l & ((1 << mm) - 1)) == 0) {
               for (int i = lane; i < n; i += 32) {
@@ -476,18 +487,16 @@ __global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out
       int take = 0;
       if (lane == 0) {
         const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_TOP, (uint64_t)depth);
-        take = u01(w.w[0]) < exp(sub_logW - logW);
+        take = u01(w.w[0]) < exp(s_ctl[5] - s_ctl[1]);
+        if (take) { s_ctl[3] = s_ctl[6]; s_ctl[4] = s_ctl[7]; }
+        s_ctl[1] = logaddexp(s_ctl[1], s_ctl[5]);
+        s_flag[5] = depth + 1;
       }
       take = __shfl_sync(0xffffffffu, take, 0);
-      if (take) {
+      if (take)
         for (int i = lane; i < n; i += 32) zc[i] = sz[i];
-        cand_lo = sub_lo;
-        cand_ln = sub_ln;
-      }
-      logW = logaddexp(logW, sub_logW);
       for (int i = lane; i < n; i += 32) rho[i] += srho[i];
       __syncwarp();
-      depth_done = depth + 1;
       const double dl = warp_dot_minv(rho, pL, minv, n, D);
       const double dr = warp_dot_minv(rho, pR, minv, n, D);
       if (lane == 0) s_flag[1] = (dl <= 0.0 || dr <= 0.0) ? 1 : 0;
@@ -499,11 +508,12 @@ __global__ void __launch_bounds__(512) k_nuts(KParams kp, int round, NutsOut out
     double* zw = kp.z + gi * (int64_t)kd;
     for (int i = lane; i < n; i += 32) zw[i] = zc[i];
     if (lane == 0) {
-      kp.ll_old[gi] = cand_lo;
-      kp.ll_new[gi] = cand_ln;
-      if (out.acc) out.acc[gi] = leaves > 0 ? sum_acc / leaves : 0.0;
+      const int leaves = s_flag[3];
+      kp.ll_old[gi] = s_ctl[3];
+      kp.ll_new[gi] = s_ctl[4];
+      if (out.acc) out.acc[gi] = leaves > 0 ? s_ctl[2] / leaves : 0.0;
       if (out.nleaf) out.nleaf[gi] = leaves;
-      if (out.flags) out.flags[gi] = diverged | (depth_done << 8);
+      if (out.flags) out.flags[gi] = s_flag[4] | (s_flag[5] << 8);
       if (kp.cs_count)   // slot 1: NUTS (initial point + every leaf)
         atomicAdd(kp.cs_count + 1, (unsigned long long)n / D * (unsigned long long)pb.n *
                                        (unsigned long long)(leaves + 1));

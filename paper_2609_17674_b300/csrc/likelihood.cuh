@@ -407,6 +407,106 @@ __device__ __forceinline__ void finish_fisher(int prec, const double* th, const 
 }
 
 // ---------------------------------------------------------------------------
+// FP32 coordinate map (mixed path; parameters whose FP32 rounding stays far
+// below the path's tolerance: amplitudes, widths, frequency derivative, phase)
+// ---------------------------------------------------------------------------
+
+struct Coord32 { float th, dth, lp, pg, pc; };
+
+__device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& pa, int d, float z) {
+  Coord32 c;
+  if (pa.model == PULSE_LINAMP) {
+    const float sd = (float)pa.amp_sd, dz = (z - (float)pa.amp_mean) / sd;
+    c.th = z; c.dth = 1.f;
+    c.lp = -0.5f * dz * dz - logf(sd) - 0.918938533204673f;
+    c.pg = -dz / sd;
+    c.pc = 1.f / (sd * sd);
+    return c;
+  }
+  // s and 1 - s both from e^{-|z|}: s (1 - s) keeps full FP32 relative precision at
+  // large |z|, where forming 1 - s by subtraction would cancel
+  const float a = fabsf(z);
+  const float e = expf(-a);
+  const float q = 1.f / (1.f + e);
+  const float s = z >= 0.f ? q : e * q;
+  const float sc = z >= 0.f ? e * q : q;
+  const float ds = s * sc;
+  if (pb.logmask & (1u << d)) {
+    const float llo = (float)pb.llo[d], span = (float)(pb.lhi[d] - pb.llo[d]);
+    c.th = expf(llo + span * s);
+    c.dth = c.th * span * ds;
+  } else {
+    const float lo = (float)pb.lo[d], span = (float)(pb.hi[d] - pb.lo[d]);
+    c.th = lo + span * s;
+    c.dth = span * ds;
+  }
+  c.lp = -a - 2.f * log1pf(e);
+  c.pg = sc - s;
+  c.pc = 2.f * ds;
+  return c;
+}
+
+// theta and dtheta/dz in FP64 for the parameters that set where a template sits
+// (pulse centre and width, sinusoid frequency): their FP32 rounding, or the FP32
+// rounding of the log-space argument of a log-uniform map, would move the template
+// by more than the path's tolerance (tails of narrow pulses, far end of the grid).
+__device__ __forceinline__ double theta64(const ProbDev& pb, int d, double z, double& dth) {
+  const double e = exp(-fabs(z));
+  const double q = 1.0 / (1.0 + e);
+  const double s = z >= 0.0 ? q : e * q;
+  const double ds = s * (z >= 0.0 ? e * q : q);
+  if (pb.logmask & (1u << d)) {
+    const double span = pb.lhi[d] - pb.llo[d];
+    const double th = exp(pb.llo[d] + span * s);
+    dth = th * span * ds;
+    return th;
+  }
+  const double span = pb.hi[d] - pb.lo[d];
+  dth = span * ds;
+  return pb.lo[d] + span * s;
+}
+
+// pulse constants from the FP64 centre and width: kappa rounded once to FP32 and used
+// for both a0 and delta, so v = (t - t0) kappa keeps its relative precision
+__device__ __forceinline__ void pulse_prep32(float A, double t0, double w, const ProbDev& pb,
+                                             float* cf) {
+  const float kap = (float)(0.84932180028801904272 / w);    // sqrt(log2(e)/2) / w
+  const double a0 = (pb.t_origin - t0) * (double)kap;
+  const double del = pb.dt * (double)kap;
+  const float a_hi = (float)a0, d_hi = (float)del;
+  cf[0] = A;
+  cf[1] = a_hi;
+  cf[2] = (float)(a0 - (double)a_hi);
+  cf[3] = d_hi;
+  cf[4] = (float)(del - (double)d_hi);
+  cf[5] = exp2f(-2.f * d_hi * d_hi);
+  cf[6] = 2.f * d_hi;
+  cf[7] = d_hi * d_hi;
+  cf[8] = del > 0.5 ? 1.0f : 0.0f;   // coarse grid: evaluate every sample directly
+}
+
+__device__ __forceinline__ void sin_prep32(float A, double f, float fd, float p0,
+                                           const ProbDev& pb, float* cf) {
+  const double to = pb.t_origin;
+  float phi = p0;
+  if (to != 0.0) {
+    double ph = ((kTwoPi * f) * to + (kPi * (double)fd) * (to * to)) + (double)p0;
+    phi = (float)remainder(ph, kTwoPi);
+  }
+  const double om = (kTwoPi * f + kTwoPi * (double)fd * to) * pb.dt;
+  const float om_hi = (float)om;
+  cf[0] = A;
+  cf[1] = phi;
+  cf[2] = om_hi;
+  cf[3] = (float)(om - (double)om_hi);
+  cf[4] = (float)(kPi * (double)fd * pb.dt * pb.dt);
+  float so, co;
+  sincosf(om_hi, &so, &co);
+  cf[5] = co;
+  cf[6] = so;
+}
+
+// ---------------------------------------------------------------------------
 // Per-component setup: theta, Jacobians, prior terms and path constants.
 // Must be called by all threads; ends with __syncthreads.  Returns the thread's
 // share of the log prior (summed by the caller's block reduction).
@@ -416,24 +516,69 @@ __device__ double eval_setup(const ProbDev& pb, const PriorArgs& pa, int K, cons
                              EvalSmem& sm) {
   constexpr int D = model_d<MODEL>();
   double lp_sum = 0.0;
-  for (int i = threadIdx.x; i < K * D; i += blockDim.x) {
-    double th, dth, lp, pg, pc;
-    coord(pb, pa, i % D, z[i], th, dth, lp, pg, pc);
-    sm.th[i] = th; sm.dth[i] = dth; sm.pg[i] = pg; sm.pc[i] = pc;
-    lp_sum += lp;
-  }
-  __syncthreads();
-  if (PREC == MIXED) {
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      const double* t = sm.th + k * D;
-      float* cf = sm.cf + k * NCF;
-      if (MODEL == SINUSOID) sin_prep(t[0], t[1], t[2], t[3], pb, cf);
-      else if (MODEL == PULSE) pulse_prep(t[0], t[1], t[2], pb, cf);
-      else pulse_prep(t[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
+  if (PREC == FP64) {
+    for (int i = threadIdx.x; i < K * D; i += blockDim.x) {
+      double th, dth, lp, pg, pc;
+      coord(pb, pa, i % D, z[i], th, dth, lp, pg, pc);
+      sm.th[i] = th; sm.dth[i] = dth; sm.pg[i] = pg; sm.pc[i] = pc;
+      lp_sum += lp;
     }
     __syncthreads();
+    return lp_sum;
   }
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double* zk = z + k * D;
+    float lp = 0.f, th[4];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const Coord32 c = coord32(pb, pa, d, (float)zk[d]);
+      th[d] = c.th;
+      sm.th[k * D + d] = (double)c.th;
+      sm.dth[k * D + d] = (double)c.dth;
+      sm.pg[k * D + d] = (double)c.pg;
+      sm.pc[k * D + d] = (double)c.pc;
+      lp += c.lp;
+    }
+    float* cf = sm.cf + k * NCF;
+    if (MODEL == SINUSOID) {
+      double dth;
+      const double f = theta64(pb, 1, zk[1], dth);
+      sm.th[k * D + 1] = f;
+      sm.dth[k * D + 1] = dth;
+      sin_prep32(th[0], f, th[2], th[3], pb, cf);
+    } else if (MODEL == PULSE) {
+      double dt0, dw;
+      const double t0 = theta64(pb, 1, zk[1], dt0);
+      const double w = theta64(pb, 2, zk[2], dw);
+      sm.th[k * D + 1] = t0;
+      sm.dth[k * D + 1] = dt0;
+      sm.th[k * D + 2] = w;
+      sm.dth[k * D + 2] = dw;
+      pulse_prep32(th[0], t0, w, pb, cf);
+    } else {
+      pulse_prep32(th[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
+    }
+    lp_sum += (double)lp;
+  }
+  __syncthreads();
   return lp_sum;
+}
+
+// Kahan step in FP32 (explicit rounding: no reassociation or contraction)
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+__device__ __forceinline__ void load_cf(const float* cf, float (&o)[NCF]) {
+  const float4* c4 = reinterpret_cast<const float4*>(cf);
+#pragma unroll
+  for (int q = 0; q < NCF / 4; ++q) {
+    const float4 v = c4[q];
+    o[4 * q] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -442,6 +587,8 @@ __device__ double eval_setup(const ProbDev& pb, const PriorArgs& pa, int K, cons
 //   grad_out[K*D] = dlogp/dz  (if GRAD; may alias shared memory)
 //   fis_out[K*D]  = Gauss-Newton diagonal + prior curvature per element (if FISHER)
 // R: samples per thread per segment (multiple of 8).
+// Mixed path: per-lane slot sums and per-thread energies are FP32 with Kahan
+// compensation across segments; the cross-warp totals are FP64.
 // ---------------------------------------------------------------------------
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
 __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
@@ -452,13 +599,18 @@ __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double
   const double lp_sum = eval_setup<MODEL, PREC>(pb, pa, K, z, sm);
 
   const int64_t N = pb.n, n1 = pb.n1;
-  const float beta_f = (float)beta, inv_s2_f = (float)pb.inv_s2;
-  double acc_old = 0.0, acc_new = 0.0;
+  double acc_old = 0.0, acc_new = 0.0;          // FP64 path
+  float eo_s = 0.f, eo_c = 0.f, en_s = 0.f, en_c = 0.f;   // mixed path energies
+  // per-lane slot sums for components k = lane (slot 0) and lane + 32 (slot 1)
+  float gs[2][4], gc[2][4], fs[2][4], fc[2][4];
   double ga[2][4], fa[2][4];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int d = 0; d < 4; ++d) { ga[s][d] = 0.0; fa[s][d] = 0.0; }
+    for (int d = 0; d < 4; ++d) {
+      gs[s][d] = gc[s][d] = fs[s][d] = fc[s][d] = 0.f;
+      ga[s][d] = fa[s][d] = 0.0;
+    }
 
   const int64_t seg = (int64_t)blockDim.x * R;
   for (int64_t base = 0; base < N; base += seg) {
@@ -467,6 +619,7 @@ __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double
     const int64_t m = base + (int64_t)tid * R;
 
     if (PREC == MIXED) {
+      const float beta_f = (float)beta, inv_s2_f = (float)pb.inv_s2;
       float r[R];
       if (m + R <= N) {
         const float4* src = reinterpret_cast<const float4*>(pb.d32 + m);
@@ -481,8 +634,9 @@ __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double
       }
       const float mf = (float)m;
       for (int k = 0; k < K; ++k) {
-        float h[R];
-        mixed_vals<MODEL, R>(sm.cf + k * NCF, mf, h);
+        float cf[NCF], h[R];
+        load_cf(sm.cf + k * NCF, cf);
+        mixed_vals<MODEL, R>(cf, mf, h);
 #pragma unroll
         for (int j = 0; j < R; ++j) r[j] -= h[j];
       }
@@ -497,21 +651,22 @@ __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double
         if (old) so += e; else sn += e;
         r[j] = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
       }
-      acc_old += (double)so;
-      acc_new += (double)sn;
+      kahan_add(eo_s, eo_c, so);
+      kahan_add(en_s, en_c, sn);
       if (GRAD) {
         for (int k = 0; k < K; ++k) {
-          float o[4];
-          mixed_adj<MODEL, R>(sm.cf + k * NCF, mf, r, o);
+          float cf[NCF], o[4];
+          load_cf(sm.cf + k * NCF, cf);
+          mixed_adj<MODEL, R>(cf, mf, r, o);
 #pragma unroll
           for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
           if (lane == (k & 31)) {
             if (k < 32) {
 #pragma unroll
-              for (int d = 0; d < D; ++d) ga[0][d] += (double)o[d];
+              for (int d = 0; d < D; ++d) kahan_add(gs[0][d], gc[0][d], o[d]);
             } else {
 #pragma unroll
-              for (int d = 0; d < D; ++d) ga[1][d] += (double)o[d];
+              for (int d = 0; d < D; ++d) kahan_add(gs[1][d], gc[1][d], o[d]);
             }
           }
         }
@@ -524,17 +679,18 @@ __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double
           cw[j] = n < N ? (n < n1 ? inv_s2_f : beta_f * inv_s2_f) : 0.0f;
         }
         for (int k = 0; k < K; ++k) {
-          float o[4];
-          mixed_fis<MODEL, R>(sm.cf + k * NCF, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
+          float cf[NCF], o[4];
+          load_cf(sm.cf + k * NCF, cf);
+          mixed_fis<MODEL, R>(cf, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
 #pragma unroll
           for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
           if (lane == (k & 31)) {
             if (k < 32) {
 #pragma unroll
-              for (int d = 0; d < D; ++d) fa[0][d] += (double)o[d];
+              for (int d = 0; d < D; ++d) kahan_add(fs[0][d], fc[0][d], o[d]);
             } else {
 #pragma unroll
-              for (int d = 0; d < D; ++d) fa[1][d] += (double)o[d];
+              for (int d = 0; d < D; ++d) kahan_add(fs[1][d], fc[1][d], o[d]);
             }
           }
         }
@@ -595,6 +751,17 @@ __device__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K, double
         }
       }
     }
+  }
+  if (PREC == MIXED) {
+    acc_old = (double)eo_s - (double)eo_c;
+    acc_new = (double)en_s - (double)en_c;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        ga[s][d] = (double)gs[s][d] - (double)gc[s][d];
+        fa[s][d] = (double)fs[s][d] - (double)fc[s][d];
+      }
   }
 
   // ---- gradient / Gauss-Newton assembly: per-warp slots -> shared -> components ----
