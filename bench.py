@@ -219,7 +219,7 @@ def run_gpu(a):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    (cs_eval, cs_nuts), launches = ctx.counters(reset=True)
+    (cs_eval, cs_nuts, cc_eval, cc_nuts), launches = ctx.counters(reset=True)
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
     ms_max = reduce(ms, dist.ReduceOp.MAX if dist else None)
@@ -229,7 +229,7 @@ def run_gpu(a):
     # roofline of the dominant kernel (NUTS transition), ALU bound (FP32 pipe)
     n_nuts, ms_nuts = prof["nuts"]
     per_launch_ms = ms_nuts / max(n_nuts, 1)
-    ops = OPS_PER_CS[wl.model] * cs_nuts
+    ops = OPS_PER_CS[wl.model] * cc_nuts       # component*samples the kernel computed
     achieved = ops / max(ms_nuts * 1e-3, 1e-12) / 1e12
     mhz = clk.get("sm_mhz") or 2032.0
     peak = FP32_LANES_PER_SM * N_SM * mhz * 1e6 / 1e12
@@ -238,6 +238,9 @@ def run_gpu(a):
             "traffic": None, "launches": n_nuts, "ms_per_launch": per_launch_ms,
             "share_of_step": ms_nuts / ms, "peak_basis": f"128 FP32 lanes x 148 SMs x {mhz:.0f} MHz"
                                                          " (median SM clock during the timed region)",
+            "ops_per_cs": OPS_PER_CS[wl.model],
+            "cs_nominal": cs_nuts, "cs_computed": cc_nuts,
+            "nominal_cs_per_s": cs_nuts / max(ms_nuts * 1e-3, 1e-12),
             "kernels_ms": {k: v[1] for k, v in prof.items()}}
 
     # end to end: population resident on the host between stages (pinned buffers)
@@ -276,7 +279,7 @@ def run_gpu(a):
             beta_h, logz_h = b, lz
         t1 = time.perf_counter()
         barrier()
-        (ce, cn), _ = ctx.counters(reset=True)
+        (ce, cn, _, _), _ = ctx.counters(reset=True)
         el = reduce(t1 - t0, dist.ReduceOp.MAX if dist else None)
         cst = reduce(float(ce + cn), dist.ReduceOp.SUM if dist else None)
         h2d = zh.numel() * 8 + Kh.numel() * 4 + 8 * 4
@@ -308,6 +311,9 @@ def run_gpu(a):
                    "N": a.samples, "P": a.particles, "kmax": 40, "K_true": 20,
                    "precision": "mixed: FP32 templates/residuals, FP64 sums/anchors/log-weights",
                    "l2": "flushed between steps (256 MB write)",
+                   "pulse_window": "on: (component, warp range) pairs with every term < 2^-49 A "
+                                   "skipped; value counts every K_p*N component*sample",
+                   "computed_fraction": (cc_eval + cc_nuts) / max(cs_eval + cs_nuts, 1),
                    "parallelism": f"{world} independent problem(s), one per GPU",
                    "stages": [stage - a.steps - (max(2, a.steps // 2) if e2e else 0), stage],
                    "beta_end": betas[-1]},

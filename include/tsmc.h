@@ -68,6 +68,11 @@ typedef struct {
   uint64_t seed;          /* Philox4x64-10 key word 0 (word 1 = problem index) */
   int32_t threads;        /* threads per particle block (32..256, multiple of 32); 0: default */
   int32_t samples_per_thread;  /* mixed path register tile: 0 (default 32), 16 or 32 */
+  int32_t pulse_window;   /* mixed pulse path: 1 skips every (component, 32-thread sample
+                             range) pair where |t - t0| > 7 w / sqrt(ln 4) throughout, i.e.
+                             all template terms < 2^-49 A (below FP32 resolution); 0 evaluates
+                             every component on every sample.  FP64 path: always 0. */
+  int32_t reserved;
 } tsmc_config;
 
 /* Workspace size for a configuration and per-problem sample capacities
@@ -172,11 +177,12 @@ tsmc_status tsmc_philox(void* ctx, const uint64_t* ctr_dev, uint64_t key0, uint6
                         int64_t n, uint64_t* out_dev);
 
 /* Statistics (no counterpart in the paper's method; measurement support):
- * cs_evals_host[2] = component*sample logL+grad evaluations done by this context's
- * kernels, the sum of K_p * N over every gradient evaluation: [0] batched
- * evaluations with a gradient, [1] NUTS (every leaf plus the initial point);
- * launches_host = kernels launched.  reset != 0 zeroes both after reading.
- * Synchronises the stream. */
+ * cs_evals_host[4] = component*sample logL+grad evaluations done by this context's
+ * kernels: [0] batched evaluations with a gradient and [1] NUTS (every leaf plus the
+ * initial point), each the sum of K_p * N_b per evaluation; [2] and [3] the same
+ * evaluations counting only the component*samples actually computed (less than
+ * [0], [1] when pulse_window skips the far tails).  launches_host = kernels launched.
+ * reset != 0 zeroes both after reading.  Synchronises the stream. */
 tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_host,
                           int32_t reset);
 

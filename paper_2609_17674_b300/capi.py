@@ -61,6 +61,7 @@ class Config(C.Structure):
         ("p_nuts", C.c_double), ("p_birth", C.c_double), ("p_death", C.c_double),
         ("amp_mean", C.c_double), ("amp_sd", C.c_double), ("seed", C.c_uint64),
         ("threads", C.c_int32), ("samples_per_thread", C.c_int32),
+        ("pulse_window", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -232,11 +233,11 @@ class Context:
         return out.cpu().numpy().view(np.uint64)
 
     def counters(self, reset=False):
-        """((batched-eval cs, NUTS cs), kernels launched) since the last reset."""
-        cs = np.zeros(2, dtype=np.uint64)
+        """((batched cs, NUTS cs, batched cs computed, NUTS cs computed), kernels launched)."""
+        cs = np.zeros(4, dtype=np.uint64)
         n = C.c_int64(0)
         self._check(self.L.tsmc_counters(self.h, _ptr(cs), C.byref(n), 1 if reset else 0))
-        return (int(cs[0]), int(cs[1])), int(n.value)
+        return tuple(int(x) for x in cs), int(n.value)
 
     def profile(self, enable=True):
         self._check(self.L.tsmc_profile(self.h, 1 if enable else 0))

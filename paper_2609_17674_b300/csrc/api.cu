@@ -97,6 +97,7 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->schedule == TSMC_SCHED_ROUNDS && !(cfg->p_birth > 0.0 && cfg->p_death > 0.0)) return TSMC_EINVAL;
   if (cfg->threads != 0 && (cfg->threads < 32 || cfg->threads > 256 || cfg->threads % 32)) return TSMC_EINVAL;
   if (cfg->samples_per_thread != 0 && cfg->samples_per_thread != 16 && cfg->samples_per_thread != 32) return TSMC_EINVAL;
+  if (cfg->pulse_window != 0 && cfg->pulse_window != 1) return TSMC_EINVAL;
   return TSMC_OK;
 }
 
@@ -134,7 +135,7 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.stats = L.take(sizeof(double) * 2 * cfg->n_problems);
   o.stage = L.take(sizeof(int32_t) * 4);
   o.tw = L.take(sizeof(double) * 2 * cfg->kmax);
-  o.cs = L.take(sizeof(unsigned long long) * 4);
+  o.cs = L.take(sizeof(unsigned long long) * 4);   // nominal / computed x batched / NUTS
   return o;
 }
 
@@ -155,6 +156,7 @@ KParams kparams(Ctx* c) {
   kp.pa.model = c->cfg.model;
   kp.pa.amp_mean = c->cfg.amp_mean;
   kp.pa.amp_sd = c->cfg.amp_sd;
+  kp.pa.window = (c->cfg.precision == TSMC_MIXED && c->cfg.pulse_window) ? 1 : 0;
   kp.seed = c->cfg.seed;
   kp.tw = c->tw;
   kp.z = c->z;
@@ -799,10 +801,11 @@ tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_
                           int32_t reset) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return TSMC_EINVAL;
-  unsigned long long v[2] = {0, 0};
+  unsigned long long v[4] = {0, 0, 0, 0};
   TRY_CUDA(c, cudaMemcpyAsync(v, c->cs_count, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
   TRY(sync_stream(c));
-  if (cs_evals_host) { cs_evals_host[0] = (uint64_t)v[0]; cs_evals_host[1] = (uint64_t)v[1]; }
+  if (cs_evals_host)
+    for (int i = 0; i < 4; ++i) cs_evals_host[i] = (uint64_t)v[i];
   if (launches_host) *launches_host = c->launches;
   if (reset) {
     TRY_CUDA(c, cudaMemsetAsync(c->cs_count, 0, sizeof(v), c->stream));

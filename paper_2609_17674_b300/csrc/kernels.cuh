@@ -2,6 +2,8 @@
 // birth/death, NUTS transitions, prior initialisation, ESS tempering,
 // systematic resampling and the population metric.
 #pragma once
+#include <type_traits>
+
 #include "likelihood.cuh"
 
 namespace tsmc {
@@ -36,7 +38,7 @@ struct SmemPlan {
            sizeof(float) * (size_t)kd * NCF + 16;
   }
   __host__ __device__ size_t nuts_bytes() const {
-    return sizeof(double) * (size_t)kd * (13 + 2 * (size_t)(depth + 1));
+    return sizeof(double) * (size_t)kd * (13 + 2 * (size_t)(depth + 1));   // 8-byte slots
   }
   // eval kernel: + gradient and Gauss-Newton staging; RJ: + proposal coordinates
   __host__ __device__ size_t eval_kernel_bytes() const {
@@ -105,8 +107,10 @@ __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) 
     double* g = io.grad + gi * (int64_t)sp.kd;
     for (int i = tid; i < sp.kd; i += blockDim.x) g[i] = i < K * D ? gbuf[i] : 0.0;
   }
-  if (GRAD && tid == 0 && kp.cs_count)
-    atomicAdd(kp.cs_count, (unsigned long long)K * (unsigned long long)pb.n);   // slot 0: batched
+  if (GRAD && tid == 0 && kp.cs_count) {   // slots 0 / 2: batched, nominal / computed
+    atomicAdd(kp.cs_count, (unsigned long long)K * (unsigned long long)pb.n);
+    atomicAdd(kp.cs_count + 2, (unsigned long long)sm.scal[3]);
+  }
   if (FISHER && io.fis_sum) {
     if (tid < D) {
       double s = 0.0;
@@ -210,29 +214,37 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   __syncthreads();
   const int kp_idx = move == 1 ? K : s_j;      // index of the proposed component
   eval_setup<MODEL, PREC>(pb, kp.pa, move == 1 ? K + 1 : K, zs, sm);
-  const int64_t N = pb.n, n1 = pb.n1;
+  const int N = (int)pb.n, n1 = (int)pb.n1;   // < 2^24 samples
   double a_old = 0.0, a_new = 0.0;
-  const int64_t seg = (int64_t)blockDim.x * R;
+  const int seg = blockDim.x * R;
   const int warp = tid >> 5;
-  for (int64_t base = 0; base < N; base += seg) {
-    if (base + (int64_t)warp * 32 * R >= N) continue;
-    const int64_t m = base + (int64_t)tid * R;
+  for (int base = 0; base < N; base += seg) {
+    const int wfirst = base + warp * 32 * R;
+    if (wfirst >= N) continue;
+    const float wf = (float)wfirst, wl = (float)(wfirst + 32 * R - 1);
+    const int m = base + tid * R;
     if (PREC == MIXED) {
+      const bool win = MODEL != SINUSOID && kp.pa.window;
+      float cfp[NCF];
+      load_cf(sm.cf + kp_idx * NCF, cfp);
+      if (win && outside_support(cfp, wf, wl)) continue;   // proposal is zero here
       float r[R], hp[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
       const float mf = (float)m;
       for (int k = 0; k < K; ++k) {
-        float h[R];
-        mixed_vals<MODEL, R>(sm.cf + k * NCF, mf, h);
+        float cf[NCF], h[R];
+        load_cf(sm.cf + k * NCF, cf);
+        if (win && outside_support(cf, wf, wl)) continue;
+        mixed_vals<MODEL, R>(cf, mf, h);
 #pragma unroll
         for (int j = 0; j < R; ++j) r[j] -= h[j];
       }
-      mixed_vals<MODEL, R>(sm.cf + kp_idx * NCF, mf, hp);
+      mixed_vals<MODEL, R>(cfp, mf, hp);
       float so = 0.f, sn = 0.f;
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int64_t n = m + j;
+        const int n = m + j;
         const float h = n < N ? hp[j] : 0.0f;
         const float t = move == 1 ? __fmaf_rn(-0.5f * h, h, r[j] * h)
                                   : -__fmaf_rn(0.5f * h, h, r[j] * h);
@@ -255,7 +267,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
       const double* thp = sm.th + kp_idx * D;
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int64_t n = m + j;
+        const int n = m + j;
         if (n >= N) continue;
         const double r = __dadd_rn(pb.d64[n], -hs[j]);
         const double h = fp64_val<MODEL>(thp, 0.0, 0.0, time_of(pb, n), nullptr);
@@ -305,19 +317,61 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
 // ---------------------------------------------------------------------------
 struct NutsOut { double* acc; int32_t* nleaf; int32_t* flags; };
 
-__device__ __forceinline__ double warp_dot_minv(const double* a, const double* b,
-                                                const double* minv, int n, int D) {
-  double s = 0.0;
+// Tree-control arithmetic: FP64 on the FP64 path (bit-level agreement with the
+// oracle), FP32 on the mixed path (momenta, U-turn sums, kinetic energy and the
+// probabilities compared with uniforms; positions, H and log-weights stay FP64).
+__device__ __forceinline__ float ct_exp(float x) { return expf(x); }
+__device__ __forceinline__ double ct_exp(double x) { return exp(x); }
+__device__ __forceinline__ float ct_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double ct_log1p(double x) { return log1p(x); }
+
+template <typename CT>
+__device__ __forceinline__ double lae(double a, double b) {   // log(e^a + e^b)
+  if (a == -INFINITY) return b;
+  if (b == -INFINITY) return a;
+  const double m = a > b ? a : b;
+  return m + (double)ct_log1p(ct_exp((CT)(-fabs(a - b))));
+}
+
+template <typename CT>
+__device__ __forceinline__ CT momentum_normal(uint64_t seed, int problem, uint64_t particle,
+                                              int stage, int round, uint64_t m);
+template <>
+__device__ __forceinline__ double momentum_normal<double>(uint64_t seed, int problem,
+                                                          uint64_t particle, int stage,
+                                                          int round, uint64_t m) {
+  return draw_normal(seed, problem, particle, stage, round, PU_MOMENTUM, m);
+}
+template <>
+__device__ __forceinline__ float momentum_normal<float>(uint64_t seed, int problem,
+                                                        uint64_t particle, int stage, int round,
+                                                        uint64_t m) {
+  // same stream and Box-Muller pairing as the FP64 path, evaluated in FP32
+  const Rand4 r = draw(seed, problem, particle, stage, round, PU_MOMENTUM, m >> 2);
+  const int pair = (int)((m & 3) >> 1);
+  const float ua = (float)u01(r.w[2 * pair]), ub = (float)u01(r.w[2 * pair + 1]);
+  const float rad = sqrtf(-2.0f * logf(ua));
+  float sn, cs;
+  sincospif(2.0f * ub, &sn, &cs);
+  return (m & 1) ? rad * sn : rad * cs;
+}
+
+template <typename CT>
+__device__ __forceinline__ CT warp_dot_minv(const CT* a, const CT* b, const CT* minv, int n,
+                                            int D) {
+  CT s = 0;
   for (int i = threadIdx.x & 31; i < n; i += 32) s += a[i] * (minv[i % D] * b[i]);
   return warp_sum(s);
 }
 
 template <int MODEL, int PREC, int R>
 __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
+  using CT = typename std::conditional<PREC == MIXED, float, double>::type;
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   __shared__ int s_flag[8];
   __shared__ double s_ctl[8];
+  __shared__ CT s_minv[4];
   const int64_t gi = blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const uint64_t li = (uint64_t)(gi % kp.P);
@@ -342,39 +396,46 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   }
   char* p = smem;
   EvalSmem sm = carve_eval(p, sp, kp.tw);
-  double* v = reinterpret_cast<double*>(p);
   const int kd = sp.kd;
-  double *zc = v, *z1 = v + kd, *p1 = v + 2 * kd, *g1 = v + 3 * kd;
-  double *zL = v + 4 * kd, *pL = v + 5 * kd, *gL = v + 6 * kd;
-  double *zR = v + 7 * kd, *pR = v + 8 * kd, *gR = v + 9 * kd;
-  double *rho = v + 10 * kd, *srho = v + 11 * kd, *sz = v + 12 * kd;
-  double* ckp = v + 13 * kd;                  // [(depth+1)][kd]
-  double* ckr = ckp + (size_t)(sp.depth + 1) * kd;
+  // positions (FP64) and the evaluation's gradient output (FP64)
+  double* vd = reinterpret_cast<double*>(p);
+  double *zc = vd, *z1 = vd + kd, *zL = vd + 2 * kd, *zR = vd + 3 * kd, *sz = vd + 4 * kd;
+  double* g1 = vd + 5 * kd;
+  // momenta, gradients at the ends, momentum sums and checkpoints (CT), one slot of
+  // 8 bytes per element each so the layout does not depend on CT
+  CT* vc = reinterpret_cast<CT*>(vd + 6 * kd);
+  const int st = (int)(sizeof(double) / sizeof(CT)) * kd;   // CT elements per slot
+  CT *p1 = vc, *pL = vc + st, *pR = vc + 2 * st, *gL = vc + 3 * st, *gR = vc + 4 * st;
+  CT *rho = vc + 5 * st, *srho = vc + 6 * st;
+  CT* ckp = vc + 7 * st;                       // [(depth+1)][kd] CT
+  CT* ckr = ckp + (size_t)(sp.depth + 1) * kd;
   const double beta = kp.beta[prob];
   const double eps = kp.eps[prob];
-  const double* minv = kp.minv + 4 * prob;
+  if (tid < 4) s_minv[tid] = (CT)kp.minv[4 * prob + tid];
+  const CT* minv = s_minv;
   const double* zg = kp.z + gi * (int64_t)kd;
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
   block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+  double cs_done = sm.scal[3];   // component*samples computed (thread 0)
   // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
   // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
   // s_ctl: 0 H0, 1 logW, 2 sum_acc, 3 cand_lo, 4 cand_ln, 5 sub_logW, 6 sub_lo, 7 sub_ln
   // s_flag: 0 subtree valid, 1 stop, 2 direction, 3 leaves, 4 diverged, 5 depth done
   if (warp == 0) {
     for (int i = lane; i < n; i += 32) {
-      const double pm = sqrt(1.0 / minv[i % D]) *
-                        draw_normal(kp.seed, prob, li, stage, round, PU_MOMENTUM, (uint64_t)i);
+      const CT pm = sqrt((CT)1 / minv[i % D]) *
+                    momentum_normal<CT>(kp.seed, prob, li, stage, round, (uint64_t)i);
       pL[i] = pm; pR[i] = pm; rho[i] = pm;
       zL[i] = zc[i]; zR[i] = zc[i];
-      gL[i] = g1[i]; gR[i] = g1[i];
+      gL[i] = (CT)g1[i]; gR[i] = (CT)g1[i];
     }
     __syncwarp();
-    double kin = 0.0;
+    CT kin = 0;
     for (int i = lane; i < n; i += 32) kin += minv[i % D] * pL[i] * pL[i];
     kin = warp_sum(kin);
     if (lane == 0) {
-      const double H0 = -sm.scal[0] + 0.5 * kin;
+      const double H0 = -sm.scal[0] + 0.5 * (double)kin;
       s_ctl[0] = H0;
       s_ctl[1] = -H0;
       s_ctl[2] = 0.0;
@@ -395,49 +456,56 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         s_flag[2] = dir;
       }
       dir = __shfl_sync(0xffffffffu, dir, 0);
-      const double *zs0 = dir > 0 ? zR : zL, *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
+      const double* zs0 = dir > 0 ? zR : zL;
+      const CT *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
       for (int i = lane; i < n; i += 32) {
-        z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0.0;
+        z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = (double)gs0[i]; srho[i] = 0;
       }
     }
     __syncthreads();
     const double de = s_flag[2] * eps;
+    const CT de_c = (CT)de;
     bool valid = true;
     for (int l = 0; l < nsub; ++l) {
       if (warp == 0) {
         for (int i = lane; i < n; i += 32) {
-          const double ph = p1[i] + 0.5 * de * g1[i];
+          const CT ph = p1[i] + (CT)0.5 * de_c * (CT)g1[i];
           p1[i] = ph;
-          z1[i] = z1[i] + de * minv[i % D] * ph;
+          if (PREC == FP64) z1[i] = z1[i] + de * (double)minv[i % D] * (double)ph;
+          else z1[i] = z1[i] + (double)(de_c * minv[i % D] * ph);
         }
       }
       __syncthreads();
       block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+      cs_done += sm.scal[3];
       if (warp == 0) {
-        double kin = 0.0;
+        CT kin = 0;
         for (int i = lane; i < n; i += 32) {
-          const double pn = p1[i] + 0.5 * de * g1[i];
+          const CT pn = p1[i] + (CT)0.5 * de_c * (CT)g1[i];
           p1[i] = pn;
           kin += minv[i % D] * pn * pn;
         }
         kin = warp_sum(kin);
-        const double H = -sm.scal[0] + 0.5 * kin;
+        const double H = -sm.scal[0] + 0.5 * (double)kin;
         const double H0 = s_ctl[0];
         int ok = 1, take = 0;
         if (lane == 0) {
           s_flag[3] += 1;
-          if (isfinite(H)) { const double a = exp(H0 - H); s_ctl[2] += a < 1.0 ? a : 1.0; }
+          if (isfinite(H)) {
+            const double a = (double)ct_exp((CT)(H0 - H));
+            s_ctl[2] += a < 1.0 ? a : 1.0;
+          }
           if (!isfinite(H) || H - H0 > 1000.0) {
             ok = 0;
             s_flag[4] = 1;
           } else {
             const double lw = -H;
-            const double nl = logaddexp(s_ctl[5], lw);
+            const double nl = lae<CT>(s_ctl[5], lw);
             take = (l == 0);
             if (!take) {
               const int leaf_id = (nsub - 1) + l;
               const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_LEAF, (uint64_t)leaf_id);
-              take = u01(w.w[0]) < exp(lw - nl);
+              take = u01(w.w[0]) < (double)ct_exp((CT)(lw - nl));
             }
             if (take) { s_ctl[6] = sm.scal[1]; s_ctl[7] = sm.scal[2]; }
             s_ctl[5] = nl;
@@ -460,16 +528,16 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
           __syncwarp();
           for (int mm = 1; mm <= depth && ok; ++mm) {
             if (((l + 1) & ((1 << mm) - 1)) == 0) {
-              double s1 = 0.0, s2 = 0.0;
+              CT s1 = 0, s2 = 0;
               for (int i = lane; i < n; i += 32) {
-                const double seg = srho[i] - ckr[mm * kd + i];
-                const double mi = minv[i % D];
+                const CT seg = srho[i] - ckr[mm * kd + i];
+                const CT mi = minv[i % D];
                 s1 += seg * (mi * ckp[mm * kd + i]);
                 s2 += seg * (mi * p1[i]);
               }
               s1 = warp_sum(s1);
               s2 = warp_sum(s2);
-              if (s1 <= 0.0 || s2 <= 0.0) ok = 0;
+              if (s1 <= 0 || s2 <= 0) ok = 0;
             }
           }
         }
@@ -482,14 +550,15 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
     if (!valid) break;
     if (warp == 0) {
       const int dir = s_flag[2];
-      double *ze = dir > 0 ? zR : zL, *pe = dir > 0 ? pR : pL, *ge = dir > 0 ? gR : gL;
-      for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = g1[i]; }
+      double* ze = dir > 0 ? zR : zL;
+      CT *pe = dir > 0 ? pR : pL, *ge = dir > 0 ? gR : gL;
+      for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = (CT)g1[i]; }
       int take = 0;
       if (lane == 0) {
         const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_TOP, (uint64_t)depth);
-        take = u01(w.w[0]) < exp(s_ctl[5] - s_ctl[1]);
+        take = u01(w.w[0]) < (double)ct_exp((CT)(s_ctl[5] - s_ctl[1]));
         if (take) { s_ctl[3] = s_ctl[6]; s_ctl[4] = s_ctl[7]; }
-        s_ctl[1] = logaddexp(s_ctl[1], s_ctl[5]);
+        s_ctl[1] = lae<CT>(s_ctl[1], s_ctl[5]);
         s_flag[5] = depth + 1;
       }
       take = __shfl_sync(0xffffffffu, take, 0);
@@ -497,9 +566,9 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         for (int i = lane; i < n; i += 32) zc[i] = sz[i];
       for (int i = lane; i < n; i += 32) rho[i] += srho[i];
       __syncwarp();
-      const double dl = warp_dot_minv(rho, pL, minv, n, D);
-      const double dr = warp_dot_minv(rho, pR, minv, n, D);
-      if (lane == 0) s_flag[1] = (dl <= 0.0 || dr <= 0.0) ? 1 : 0;
+      const CT dl = warp_dot_minv<CT>(rho, pL, minv, n, D);
+      const CT dr = warp_dot_minv<CT>(rho, pR, minv, n, D);
+      if (lane == 0) s_flag[1] = (dl <= 0 || dr <= 0) ? 1 : 0;
     }
     __syncthreads();
     if (s_flag[1]) break;
@@ -514,12 +583,13 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       if (out.acc) out.acc[gi] = leaves > 0 ? s_ctl[2] / leaves : 0.0;
       if (out.nleaf) out.nleaf[gi] = leaves;
       if (out.flags) out.flags[gi] = s_flag[4] | (s_flag[5] << 8);
-      if (kp.cs_count)   // slot 1: NUTS (initial point + every leaf)
+      if (kp.cs_count) {  // slots 1 / 3: NUTS (initial point + every leaf), nominal / computed
         atomicAdd(kp.cs_count + 1, (unsigned long long)n / D * (unsigned long long)pb.n *
                                        (unsigned long long)(leaves + 1));
+        atomicAdd(kp.cs_count + 3, (unsigned long long)cs_done);
+      }
     }
   }
-  (void)s_ctl;
 }
 
 // ---------------------------------------------------------------------------

@@ -14,19 +14,20 @@ from .synth import Workload
 
 
 def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
-                samples_per_thread: int = 0) -> capi.Config:
+                samples_per_thread: int = 0, pulse_window: int = 1) -> capi.Config:
     return capi.Config(model=wl.model, precision=precision, schedule=wl.schedule,
                        n_problems=len(wl.problems), particles=wl.P, kmax=wl.kmax,
                        n_mut=wl.n_mut, max_depth=wl.max_depth, alpha=wl.alpha, p_nuts=wl.p_nuts,
                        p_birth=wl.p_birth, p_death=wl.p_death, amp_mean=wl.amp_mean,
                        amp_sd=wl.amp_sd, seed=wl.seed, threads=threads,
-                       samples_per_thread=samples_per_thread)
+                       samples_per_thread=samples_per_thread,
+                       pulse_window=pulse_window if precision == capi.MIXED else 0)
 
 
 def open_context(wl: Workload, precision=capi.MIXED, n_use=None, n_capacity=None, threads=0,
-                 samples_per_thread=0, stream=None) -> capi.Context:
+                 samples_per_thread=0, stream=None, pulse_window=1) -> capi.Context:
     """Context with every problem's data uploaded (first n_use samples of each)."""
-    cfg = make_config(wl, precision, threads, samples_per_thread)
+    cfg = make_config(wl, precision, threads, samples_per_thread, pulse_window)
     nb = len(wl.problems)
     n_use = n_use or [p.n for p in wl.problems]
     if np.isscalar(n_use):

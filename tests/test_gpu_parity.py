@@ -334,3 +334,24 @@ def test_bad_arguments_rejected():
     with pytest.raises(capi.TsmcError):
         ctx.set_population(dev_tensor(np.zeros((512, 10, 3))),
                            dev_tensor(np.full(512, 11, np.int32)))
+
+
+def test_pulse_window_matches_full_evaluation():
+    """The support window changes nothing beyond FP32 resolution and skips real work."""
+    t = torch()
+    wl = synth.config2(P=256)
+    z, K = population(wl, 4, 256)
+    out = []
+    for win in (0, 1):
+        ctx = sampler.open_context(wl, capi.MIXED, pulse_window=win)
+        zd, Kd = dev_tensor(z, t.float64), dev_tensor(K, t.int32)
+        ctx.set_population(zd, Kd, beta=[0.3])
+        ctx.counters(reset=True)
+        lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.3], t.float64), grad=True)
+        (nom, _, comp, _), _ = ctx.counters()
+        out.append((ln.cpu().numpy(), g.cpu().numpy(), nom, comp))
+    (l0, g0, n0, c0), (l1, g1, n1, c1) = out
+    assert n0 == n1 == c0 and c1 < 0.7 * n1
+    np.testing.assert_allclose(l1, l0, rtol=1e-6)
+    res = oracle.Oracle(wl).logl_grad(z[:8], K[:8], 0.3)
+    assert np.all(np.abs(g1[:8] - g0[:8]) <= 1e-5 * res["gscale"] + 1e-300)
