@@ -1,5 +1,6 @@
 // api.cu -- host side of libtsmc: the C ABI of include/tsmc.h over a
 // caller-owned device workspace, kernel dispatch and the stage driver.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,9 @@ struct Ctx {
   double* tw = nullptr;
   double* host_out = nullptr;  // pinned? plain host staging for small reads
   unsigned long long* cs_count = nullptr;
+  int32_t* order = nullptr;      // [Ptot] launch order of particle blocks
+  int32_t* order_hist = nullptr; // [kOrderBuckets] bucket counts / offsets (scratch)
+  double nmax = 1.0;             // largest problem capacity (cost normalisation)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   int64_t graph_kernels = 0;
@@ -85,7 +89,7 @@ struct Layout {
 
 struct Offsets {
   size_t probs, d64, d32, z, z2, K, K2, llo, llo2, lln, lln2, logw, cw, anc, acc, nleaf, flags,
-      outcome, fis, beta, logz, ess, eps, minv, stats, stage, tw, cs;
+      outcome, fis, beta, logz, ess, eps, minv, stats, stage, tw, cs, order, order_hist;
 };
 
 tsmc_status check_cfg(const tsmc_config* cfg) {
@@ -136,6 +140,8 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.stage = L.take(sizeof(int32_t) * 4);
   o.tw = L.take(sizeof(double) * 2 * cfg->kmax);
   o.cs = L.take(sizeof(unsigned long long) * 4);   // nominal / computed x batched / NUTS
+  o.order = L.take(sizeof(int32_t) * Ptot);
+  o.order_hist = L.take(sizeof(int32_t) * kOrderBuckets);
   return o;
 }
 
@@ -168,6 +174,7 @@ KParams kparams(Ctx* c) {
   kp.minv = c->minv;
   kp.stage = c->stage;
   kp.cs_count = c->cs_count;
+  kp.order = nullptr;
   return kp;
 }
 
@@ -239,10 +246,29 @@ tsmc_status post(Ctx* c, const char* what) {
 
 tsmc_status last_launch(Ctx* c, const char* what) { return post(c, what); }
 
+// longest-first order of the particle blocks for population K (device array)
+tsmc_status build_order(Ctx* c, const int32_t* K) {
+  TRY_CUDA(c, cudaMemsetAsync(c->order_hist, 0, sizeof(int32_t) * kOrderBuckets, c->stream));
+  const unsigned nb = (unsigned)((c->Ptot + 255) / 256);
+  pre(c, KC_OTHER);
+  k_order_count<<<nb, 256, 0, c->stream>>>(K, c->probs, c->cfg.particles, c->cfg.kmax, c->nmax,
+                                           c->Ptot, c->order_hist);
+  TRY(post(c, "k_order_count"));
+  pre(c, KC_OTHER);
+  k_order_scan<<<1, kOrderBuckets, 0, c->stream>>>(c->order_hist);
+  TRY(post(c, "k_order_scan"));
+  pre(c, KC_OTHER);
+  k_order_scatter<<<nb, 256, 0, c->stream>>>(K, c->probs, c->cfg.particles, c->cfg.kmax, c->nmax,
+                                             c->Ptot, c->order_hist, c->order);
+  return post(c, "k_order_scatter");
+}
+
 // ---- dispatch on (model, precision, samples per thread) ----
 template <int MODEL, int PREC, int R>
 tsmc_status eval_launch_t(Ctx* c, const EvalIO& io, bool grad, bool fisher) {
+  TRY(build_order(c, io.K));
   KParams kp = kparams(c);
+  kp.order = c->order;
   SmemPlan sp = smem_plan(c, fisher, 0);
   const size_t sm = sp.eval_kernel_bytes();
   const dim3 grid((unsigned)c->Ptot), block(c->T);
@@ -279,7 +305,9 @@ tsmc_status rj_launch_t(Ctx* c, int round, int32_t* outcome) {
 
 template <int MODEL, int PREC, int R>
 tsmc_status nuts_launch_t(Ctx* c, int round, NutsOut out) {
+  TRY(build_order(c, c->K));
   KParams kp = kparams(c);
+  kp.order = c->order;
   SmemPlan sp = smem_plan(c, false, c->cfg.max_depth);
   const size_t sm = sp.nuts_kernel_bytes();
   auto fn = &k_nuts<MODEL, PREC, R>;
@@ -472,6 +500,9 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->stage = reinterpret_cast<int32_t*>(b + o.stage);
   c->tw = reinterpret_cast<double*>(b + o.tw);
   c->cs_count = reinterpret_cast<unsigned long long*>(b + o.cs);
+  c->order = reinterpret_cast<int32_t*>(b + o.order);
+  c->order_hist = reinterpret_cast<int32_t*>(b + o.order_hist);
+  for (int p = 0; p < cfg->n_problems; ++p) c->nmax = std::max(c->nmax, (double)cap[p]);
   c->cap.assign(cap, cap + cfg->n_problems);
   c->off.resize(cfg->n_problems);
   int64_t acc = 0;

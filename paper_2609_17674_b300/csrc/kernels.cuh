@@ -25,6 +25,7 @@ struct KParams {
   const double* minv;        // [n_problems][4]
   const int32_t* stage;      // device stage counter (graph-stable)
   unsigned long long* cs_count;  // component*sample logL+grad evaluations (statistic)
+  const int32_t* order;      // block -> particle (longest first), or null for identity
 };
 
 // Shared-memory carve for one particle block.
@@ -86,7 +87,7 @@ template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
 __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
-  const int64_t gi = blockIdx.x;
+  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const ProbDev pb = kp.probs[prob];
   char* p = smem;
@@ -160,7 +161,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   __shared__ int s_j;
   __shared__ double s_u;
   __shared__ double s_znew[4];
-  const int64_t gi = blockIdx.x;
+  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const uint64_t li = (uint64_t)(gi % kp.P);
   const ProbDev pb = kp.probs[prob];
@@ -372,7 +373,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   __shared__ int s_flag[8];
   __shared__ double s_ctl[8];
   __shared__ CT s_minv[4];
-  const int64_t gi = blockIdx.x;
+  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const uint64_t li = (uint64_t)(gi % kp.P);
   const ProbDev pb = kp.probs[prob];
@@ -807,6 +808,50 @@ __global__ void k_eps_update(const ProbDev* probs, double* stats, double* eps, i
   }
   stats[2 * prob] = 0.0;
   stats[2 * prob + 1] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Longest-first launch order: particle blocks sorted by cost K_p * N_b (bucketed,
+// descending) so the largest blocks start first and the last wave is short.
+// ---------------------------------------------------------------------------
+constexpr int kOrderBuckets = 1024;
+
+__device__ __forceinline__ int order_key(const int32_t* K, const ProbDev* probs, int64_t i, int P,
+                                         int kmax, double nmax) {
+  const int prob = (int)(i / P);
+  const int k = min(max(K[i], 0), kmax);
+  const double cost = (double)k * (double)probs[prob].n / ((double)kmax * nmax);  // in [0, 1]
+  const int b = min(kOrderBuckets - 1, (int)(cost * (kOrderBuckets - 1) + 0.5));
+  return kOrderBuckets - 1 - b;   // ascending key = descending cost
+}
+
+__global__ void k_order_count(const int32_t* K, const ProbDev* probs, int P, int kmax, double nmax,
+                              int64_t Ptot, int32_t* hist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Ptot) atomicAdd(&hist[order_key(K, probs, i, P, kmax, nmax)], 1);
+}
+
+__global__ void k_order_scan(int32_t* hist) {   // one block of kOrderBuckets threads
+  __shared__ int32_t s[kOrderBuckets];
+  const int t = threadIdx.x;
+  s[t] = hist[t];
+  __syncthreads();
+  for (int o = 1; o < kOrderBuckets; o <<= 1) {
+    const int32_t v = t >= o ? s[t - o] : 0;
+    __syncthreads();
+    s[t] += v;
+    __syncthreads();
+  }
+  hist[t] = t == 0 ? 0 : s[t - 1];   // exclusive offsets
+}
+
+__global__ void k_order_scatter(const int32_t* K, const ProbDev* probs, int P, int kmax,
+                                double nmax, int64_t Ptot, int32_t* offsets, int32_t* order) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Ptot) {
+    const int pos = atomicAdd(&offsets[order_key(K, probs, i, P, kmax, nmax)], 1);
+    order[pos] = (int32_t)i;
+  }
 }
 
 __global__ void k_set_int(int32_t* p, int v) { *p = v; }
