@@ -1,0 +1,76 @@
+"""Whole-SMC statistical parity on the N=1024 pulse workload (P=512, K ~ U{0..10}).
+
+Twenty prior-start runs on the GPU (Philox seeds 0..19, FP64 and mixed paths) are
+compared with twenty oracle runs with the same seeds (tests/golden/
+smc_config1_oracle.json, written by make_smc_config1.py from the oracle alone):
+the K-posterior histogram, log Z and the label-invariant summaries (sorted pulse
+centres and amplitudes among particles with K = K_true) agree within 3 Monte-Carlo
+standard errors.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2609_17674_b300 import capi, sampler, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "smc_config1_oracle.json")
+
+
+def _gpu_runs(prec, seeds):
+    import torch
+
+    sys_path = os.path.join(os.path.dirname(__file__), "golden")
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(sys_path, "make_smc_config1.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    runs = []
+    for s in seeds:
+        wl = synth.config1()
+        wl.seed = s
+        ctx = sampler.open_context(wl, prec)
+        out = sampler.run_smc(ctx, max_stages=400)
+        z, K, _, _ = ctx.get_population()
+        r = mk.summaries(wl, z.cpu().numpy(), K.cpu().numpy())
+        r["logz"] = float(out["logz"][-1][0])
+        r["n_stages"] = out["n_stages"]
+        r["beta_last"] = float(out["beta"][-1][0])
+        runs.append(r)
+        ctx.close()
+    return runs
+
+
+def _mean_se(x):
+    x = np.asarray(x, dtype=float)
+    return x.mean(0), x.std(0, ddof=1) / math.sqrt(len(x))
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_smc_matches_oracle_within_3_se(prec):
+    gold = json.load(open(GOLDEN))["runs"]
+    gpu = _gpu_runs(prec, [r["seed"] for r in gold])
+    assert all(r["beta_last"] == 1.0 for r in gpu)
+    # K histogram, bin by bin
+    hg, sg = _mean_se([r["hist"] for r in gpu])
+    ho, so = _mean_se([r["hist"] for r in gold])
+    bound = 3 * np.sqrt(sg**2 + so**2) + 0.01
+    assert np.all(np.abs(hg - ho) <= bound), (hg, ho, bound)
+    # evidence
+    lg, slg = _mean_se([r["logz"] for r in gpu])
+    lo, slo = _mean_se([r["logz"] for r in gold])
+    assert abs(lg - lo) <= 3 * math.hypot(slg, slo) + 0.02, (lg, lo, slg, slo)
+    # label-invariant parameter summaries among K = K_true particles
+    for key in ("t0_sorted_mean", "A_by_t0_mean"):
+        xg = [r[key] for r in gpu if key in r]
+        xo = [r[key] for r in gold if key in r]
+        mg, seg = _mean_se(xg)
+        mo, seo = _mean_se(xo)
+        assert np.all(np.abs(mg - mo) <= 3 * np.sqrt(seg**2 + seo**2) + 1e-4), (key, mg, mo)
+    # the run length (number of tempering stages) is a property of the same method
+    assert abs(np.mean([r["n_stages"] for r in gpu]) - np.mean([r["n_stages"] for r in gold])) <= 2
