@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--samples", type=int, default=16384)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--clock-ms", type=int, default=500,
+                    help="nvidia-smi sampling interval (200 ms polling slows kernels on this part)")
+    ap.add_argument("--clock-fields", default="full", choices=["full", "clocks"])
     return ap.parse_args()
 
 
@@ -137,12 +140,14 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 200, fields: str = "full"):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = self.FIELDS if fields == "full" else "index,clocks.sm,clocks.max.sm"
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200", "-i",
-                                       str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms",
+                                       str(interval_ms), "-i", str(gpu_index)],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
@@ -153,7 +158,8 @@ class ClockSampler:
         self.p.wait()
         self.f.flush()
         self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 2]
+        rows = [r + ["Not Active"] * (9 - len(r)) for r in rows]
         os.unlink(self.f.name)
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
@@ -199,23 +205,22 @@ def run_gpu(a):
     for _ in range(a.warmup):
         ctx.run_stage(stage, use_graph=False)
         stage += 1
-    ctx.profile(True)
+    ctx.profile(True, events=200 * a.steps)
     ctx.counters(reset=True)
     ctx.profile_read(reset=True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, a.clock_ms, a.clock_fields)
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    betas = []
     for _ in range(a.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)          # L2 flush between steps (256 MB write)
-        b, lz, e = ctx.run_stage(stage, use_graph=False)
-        betas.append(float(b[0]))
+        ctx.run_stage(stage, use_graph=False, read=False)   # queued: no host sync per stage
         stage += 1
     ev1.record(stream)
     torch.cuda.synchronize()
+    betas = [float(ctx.temper_state()[0][0])]
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)

@@ -151,17 +151,23 @@ tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_host, double* minv_hos
 tsmc_status tsmc_update_metric(void* ctx);
 
 /* Choose beta by ESS bisection, reweight (evidence increment) and resample
- * systematically (Sec. 2 steps 1-2).  Host outputs (nullable) [n_problems]. */
+ * systematically (Sec. 2 steps 1-2).  Host outputs (nullable) [n_problems]; with
+ * all three NULL the call does not synchronise. */
 tsmc_status tsmc_temper_reweight_resample(void* ctx, int32_t stage, double* beta_host,
                                           double* logz_host, double* ess_host);
+/* Current beta, log Z and last ESS per problem (host [n_problems], nullable);
+ * synchronises the stream. */
+tsmc_status tsmc_get_state(void* ctx, double* beta_host, double* logz_host, double* ess_host);
+
 /* Ancestors of the last resampling, [P_total] local indices (test access). */
 tsmc_status tsmc_get_ancestors(void* ctx, int32_t* anc_dev);
 
 /* One whole stage: temper/reweight/resample, metric, n_mut mutation rounds,
  * step-size update eps <- eps exp(mean_acc - 0.8) clamped to [1e-4, 2].
  * Problems already at beta = 1 before the stage are skipped.  Host outputs
- * (nullable) [n_problems].  Uses a CUDA graph for the mutation rounds when
- * use_graph != 0. */
+ * (nullable) [n_problems]; with all three NULL the call does not synchronise
+ * (stages can be queued back to back).  Uses a CUDA graph for the mutation rounds
+ * when use_graph != 0 and the stream is not the legacy default stream. */
 tsmc_status tsmc_run_stage(void* ctx, int32_t stage, int32_t use_graph, double* beta_host,
                            double* logz_host, double* ess_host);
 
@@ -190,7 +196,8 @@ tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_
  * on).  Classes: 0 eval, 1 rj, 2 nuts, 3 temper, 4 resample, 5 gather, 6 metric,
  * 7 other.  tsmc_profile_read fills launches_host[8] and ms_host[8] (device time
  * between events recorded on the context stream around each launch) and
- * synchronises the stream; reset != 0 forgets the records. */
+ * synchronises the stream; reset != 0 forgets the records.  enable > 1 also
+ * creates that many events up front (two per recorded launch). */
 tsmc_status tsmc_profile(void* ctx, int32_t enable);
 tsmc_status tsmc_profile_read(void* ctx, int64_t* launches_host, double* ms_host, int32_t reset);
 

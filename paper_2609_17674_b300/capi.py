@@ -40,6 +40,7 @@ SIGNATURES = {
     "tsmc_get_kernel_params": (I32, [P, P, P]),
     "tsmc_update_metric": (I32, [P]),
     "tsmc_temper_reweight_resample": (I32, [P, I32, P, P, P]),
+    "tsmc_get_state": (I32, [P, P, P, P]),
     "tsmc_get_ancestors": (I32, [P, P]),
     "tsmc_run_stage": (I32, [P, I32, I32, P, P, P]),
     "tsmc_assimilate": (I32, [P, I32, P, I64]),
@@ -207,13 +208,24 @@ class Context:
         self._check(self.L.tsmc_temper_reweight_resample(self.h, stage, _ptr(b), _ptr(lz), _ptr(e)))
         return b, lz, e
 
+    def temper_state(self):
+        """(beta, log Z, last ESS) per problem."""
+        b, lz, e = (np.zeros(self.cfg.n_problems) for _ in range(3))
+        self._check(self.L.tsmc_get_state(self.h, _ptr(b), _ptr(lz), _ptr(e)))
+        return b, lz, e
+
     def get_ancestors(self):
         a = self.torch.empty(self.P_total, dtype=self.torch.int32, device=self.ws.device)
         self._check(self.L.tsmc_get_ancestors(self.h, _ptr(a)))
         self.sync()
         return a
 
-    def run_stage(self, stage, use_graph=True):
+    def run_stage(self, stage, use_graph=True, read=True):
+        """One stage; read=False queues it without synchronising (returns None)."""
+        if not read:
+            self._check(self.L.tsmc_run_stage(self.h, stage, 1 if use_graph else 0, None, None,
+                                              None))
+            return None
         b, lz, e = (np.zeros(self.cfg.n_problems) for _ in range(3))
         self._check(self.L.tsmc_run_stage(self.h, stage, 1 if use_graph else 0, _ptr(b), _ptr(lz),
                                           _ptr(e)))
@@ -239,8 +251,9 @@ class Context:
         self._check(self.L.tsmc_counters(self.h, _ptr(cs), C.byref(n), 1 if reset else 0))
         return tuple(int(x) for x in cs), int(n.value)
 
-    def profile(self, enable=True):
-        self._check(self.L.tsmc_profile(self.h, 1 if enable else 0))
+    def profile(self, enable=True, events=0):
+        """Per-kernel-class event timing; events > 0 pre-creates that many events."""
+        self._check(self.L.tsmc_profile(self.h, max(int(events), 1) if enable else 0))
 
     def profile_read(self, reset=True):
         n = np.zeros(8, dtype=np.int64)

@@ -425,6 +425,7 @@ tsmc_status temper_resample(Ctx* c, int stage) {
 
 tsmc_status read_problem_scalars(Ctx* c, double* beta_h, double* logz_h, double* ess_h) {
   const int np = c->cfg.n_problems;
+  if (!beta_h && !logz_h && !ess_h) return TSMC_OK;   // nothing to read: stay asynchronous
   if (beta_h) TRY_CUDA(c, cudaMemcpyAsync(beta_h, c->beta, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
   if (logz_h) TRY_CUDA(c, cudaMemcpyAsync(logz_h, c->logz, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
   if (ess_h) TRY_CUDA(c, cudaMemcpyAsync(ess_h, c->ess, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
@@ -754,6 +755,13 @@ tsmc_status tsmc_temper_reweight_resample(void* ctx, int32_t stage, double* beta
   return read_problem_scalars(c, beta_h, logz_h, ess_h);
 }
 
+tsmc_status tsmc_get_state(void* ctx, double* beta_h, double* logz_h, double* ess_h) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return TSMC_EINVAL;
+  TRY(read_problem_scalars(c, beta_h, logz_h, ess_h));
+  return sync_stream(c);
+}
+
 tsmc_status tsmc_get_ancestors(void* ctx, int32_t* anc_dev) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !anc_dev) return TSMC_EINVAL;
@@ -850,6 +858,12 @@ tsmc_status tsmc_profile(void* ctx, int32_t enable) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return TSMC_EINVAL;
   c->profiling = enable != 0;
+  // create the events up front: no driver object creation inside a timed region
+  while (c->profiling && (int64_t)c->pool.size() < std::max<int64_t>(enable, 0)) {
+    cudaEvent_t e = nullptr;
+    TRY_CUDA(c, cudaEventCreate(&e));
+    c->pool.push_back(e);
+  }
   return TSMC_OK;
 }
 
