@@ -201,6 +201,37 @@ tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_
 tsmc_status tsmc_profile(void* ctx, int32_t enable);
 tsmc_status tsmc_profile_read(void* ctx, int64_t* launches_host, double* ms_host, int32_t reset);
 
+/* Systematic resampling without any device allocation and without a context.
+ *
+ * The paper has no counterpart: this is a packaging variant of the resampling
+ * step of tsmc_temper_reweight_resample for callers that cannot allocate device
+ * memory and cannot hold a caller-sized workspace -- e.g. code running while a
+ * stream is being captured into a CUDA graph (a cudaMalloc there breaks the
+ * capture), host frameworks that hand all device memory to their own pool at
+ * start-up, or latency-bound loops that must not take cudaMalloc's implicit
+ * device synchronisation.  The caller still owns the input and output buffers.
+ *
+ *   logw_dev       [n_problems * particles] FP64 log-weights (any finite shift)
+ *   ancestors_dev  [n_problems * particles] int32 output, local indices per problem:
+ *                  a_i = min{j : C_j > (i + U) / P C_P}, C the prefix sums of
+ *                  exp(logw - max), U from Philox key (seed, problem), counter
+ *                  (0, stage, purpose 7, 0) -- the same draw and arithmetic as the
+ *                  context path, so the results are identical.
+ *   cuda_stream    cudaStream_t the kernel is launched on (NULL: legacy stream).
+ *
+ * Limits: n_problems * particles <= 65536 and n_problems <= 256; larger sizes are
+ * rejected with TSMC_EINVAL (message in tsmc_last_error(NULL)).  The scratch is a
+ * fixed 512 KB file-scope device array (plus 256 all-zero problem descriptors)
+ * that every GPU which loads the library keeps until the process exits.  The
+ * first call on a device looks up the arrays' device addresses
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the same scratch and the kernel
+ * overwrites it before reading it; calls whose kernels overlap on the GPU (for
+ * example on two streams) race on it.  Asynchronous: no synchronisation. */
+tsmc_status tsmc_resample_systematic_static(const double* logw_dev, int32_t n_problems,
+                                            int32_t particles, uint64_t seed, int32_t stage,
+                                            int32_t* ancestors_dev, void* cuda_stream);
+
 /* Waits for the stream; returns TSMC_ECUDA with a message on an asynchronous error. */
 tsmc_status tsmc_sync(void* ctx);
 

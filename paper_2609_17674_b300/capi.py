@@ -48,6 +48,7 @@ SIGNATURES = {
     "tsmc_counters": (I32, [P, P, P, I32]),
     "tsmc_profile": (I32, [P, I32]),
     "tsmc_profile_read": (I32, [P, P, P, I32]),
+    "tsmc_resample_systematic_static": (I32, [P, I32, I32, U64, I32, P, P]),
     "tsmc_sync": (I32, [P]),
 }
 
@@ -92,6 +93,16 @@ def _ptr(t):
     if isinstance(t, np.ndarray):
         return t.ctypes.data
     return t.data_ptr()
+
+
+def resample_systematic_static(logw, n_problems, particles, seed, stage, ancestors, stream):
+    """Allocation-free systematic resampling (static device scratch); see include/tsmc.h."""
+    L = lib()
+    st = L.tsmc_resample_systematic_static(_ptr(logw), n_problems, particles, seed, stage,
+                                           _ptr(ancestors), stream.cuda_stream)
+    if st != OK:
+        msg = L.tsmc_last_error(None)
+        raise TsmcError(f"tsmc error {st}: {msg.decode() if msg else ''}")
 
 
 class Context:

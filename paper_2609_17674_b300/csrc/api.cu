@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -887,6 +888,74 @@ tsmc_status tsmc_profile_read(void* ctx, int64_t* launches_host, double* ms_host
     for (const Ctx::Rec& r : c->recs) { c->pool.push_back(r.a); c->pool.push_back(r.b); }
     c->recs.clear();
   }
+  return TSMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free systematic resampling.  Scratch (the FP64 prefix sums and a
+// block of all-zero problem descriptors, i.e. no problem marked done) lives in
+// file-scope device arrays that every GPU loading this library keeps until exit.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+#define TSMC_STATIC_MAX_PARTICLES 65536   /* n_problems * particles: 512 KB of prefix sums */
+#define TSMC_STATIC_MAX_PROBLEMS 256
+
+static __device__ __align__(256) double g_static_prefix[TSMC_STATIC_MAX_PARTICLES];
+static __device__ __align__(256) ProbDev g_static_probs[TSMC_STATIC_MAX_PROBLEMS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_prefix_dev[kMaxDevices] = {};
+ProbDev* g_static_probs_dev[kMaxDevices] = {};
+
+// device addresses of the static arrays for the current device (looked up once per device)
+tsmc_status static_scratch(double** prefix, ProbDev** probs) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, TSMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, TSMC_EINVAL, "device index beyond 63");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_prefix_dev[dev]) {
+    void* a = nullptr;
+    void* b = nullptr;
+    e = cudaGetSymbolAddress(&a, g_static_prefix);
+    if (e != cudaSuccess)
+      return fail(nullptr, TSMC_ECUDA, std::string("cudaGetSymbolAddress(prefix): ") + cudaGetErrorString(e));
+    e = cudaGetSymbolAddress(&b, g_static_probs);
+    if (e != cudaSuccess)
+      return fail(nullptr, TSMC_ECUDA, std::string("cudaGetSymbolAddress(problems): ") + cudaGetErrorString(e));
+    g_static_prefix_dev[dev] = static_cast<double*>(a);
+    g_static_probs_dev[dev] = static_cast<ProbDev*>(b);
+  }
+  *prefix = g_static_prefix_dev[dev];
+  *probs = g_static_probs_dev[dev];
+  return TSMC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tsmc_status tsmc_resample_systematic_static(const double* logw_dev, int32_t n_problems,
+                                            int32_t particles, uint64_t seed, int32_t stage,
+                                            int32_t* ancestors_dev, void* cuda_stream) {
+  if (!logw_dev || !ancestors_dev) return fail(nullptr, TSMC_EINVAL, "null log-weights or ancestors");
+  if (n_problems < 1 || particles < 1 || stage < 0)
+    return fail(nullptr, TSMC_EINVAL, "need n_problems >= 1, particles >= 1, stage >= 0");
+  if (n_problems > TSMC_STATIC_MAX_PROBLEMS)
+    return fail(nullptr, TSMC_EINVAL, "n_problems above the static limit of 256");
+  if ((int64_t)n_problems * particles > TSMC_STATIC_MAX_PARTICLES)
+    return fail(nullptr, TSMC_EINVAL,
+                "n_problems * particles above the static scratch limit of 65536");
+  double* prefix = nullptr;
+  ProbDev* probs = nullptr;
+  TRY(static_scratch(&prefix, &probs));
+  const int tt = particles >= 1024 ? 1024 : ((particles + 31) / 32) * 32;
+  k_resample<<<n_problems, tt, 0, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(
+      logw_dev, prefix, ancestors_dev, probs, seed, stage, particles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, TSMC_ECUDA, std::string("k_resample: ") + cudaGetErrorString(e));
   return TSMC_OK;
 }
 
