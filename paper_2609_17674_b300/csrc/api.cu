@@ -433,6 +433,11 @@ tsmc_status read_problem_scalars(Ctx* c, double* beta_h, double* logz_h, double*
   return sync_stream(c);
 }
 
+float2 split_df(double x) {   // x = hi + lo with hi the FP32 rounding of x
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
 bool all_finite(const double* a, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(a[i])) return false;
@@ -578,7 +583,12 @@ tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, i
       return fail(c, TSMC_EINVAL, "log-uniform prior needs lo > 0");
     pd.llo[d] = (logmask >> d & 1u) ? std::log(pd.lo[d]) : 0.0;
     pd.lhi[d] = (logmask >> d & 1u) ? std::log(pd.hi[d]) : 0.0;
+    const bool lg = logmask >> d & 1u;
+    pd.f_off[d] = split_df(lg ? pd.llo[d] : pd.lo[d]);
+    pd.f_span[d] = split_df(lg ? pd.lhi[d] - pd.llo[d] : pd.hi[d] - pd.lo[d]);
   }
+  pd.f_to = split_df(t_origin);
+  pd.f_dt = split_df(dt);
   TRY_CUDA(c, cudaMemcpyAsync(const_cast<double*>(pd.d64), d_host, sizeof(double) * n,
                               cudaMemcpyHostToDevice, c->stream));
   pre(c, KC_OTHER);

@@ -77,6 +77,9 @@ struct ProbDev {
   double lo[4], hi[4], llo[4], lhi[4];
   uint32_t logmask;
   int32_t done;      // beta reached 1 in an earlier stage: skipped by stage kernels
+  // double-float (hi, lo) copies for FP32 arithmetic on the mixed path:
+  // t_origin, dt, and per parameter the map's offset and span (log-space if log-uniform)
+  float2 f_to, f_dt, f_off[4], f_span[4];
 };
 
 // ---------------------------------------------------------------------------

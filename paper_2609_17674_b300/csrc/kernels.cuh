@@ -35,7 +35,7 @@ struct SmemPlan {
   int depth;       // NUTS checkpoint levels (0 for non-NUTS kernels)
   bool fisher;
   __host__ __device__ size_t eval_bytes() const {
-    return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4) +
+    return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4 + 64) +
            sizeof(float) * (size_t)kd * NCF + 16;
   }
   __host__ __device__ size_t nuts_bytes() const {
@@ -62,6 +62,7 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
   if (sp.fisher) { sm.wfis = d; d += (size_t)sp.nw * sp.kd; } else { sm.wfis = nullptr; }
   sm.red = d; d += 128;
   sm.scal = d; d += 4;
+  sm.exptab = reinterpret_cast<float2*>(d); d += 64;
   if (reinterpret_cast<uintptr_t>(d) & 8) d += 1;   // float4 loads of the constants
   sm.cf = reinterpret_cast<float*>(d);
   p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kd * NCF);
@@ -97,6 +98,8 @@ __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) 
   const int K = min(max(io.K[gi], 0), kp.kmax);   // caller array: clamp to the slots
   const double beta = io.beta[prob];
   const double* z = io.z + gi * (int64_t)sp.kd;
+  if (PREC == MIXED) fill_exp_table(sm.exptab);
+  __syncthreads();
   block_eval<MODEL, PREC, R, GRAD, FISHER>(pb, kp.pa, K, beta, z, sm, gbuf, fbuf);
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -210,6 +213,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   EvalSmem sm = carve_eval(p, sp, kp.tw);
   double* zs = reinterpret_cast<double*>(p);    // [kd + D]
   const double* zg = kp.z + gi * (int64_t)sp.kd;
+  if (PREC == MIXED) fill_exp_table(sm.exptab);
   for (int i = tid; i < K * D; i += blockDim.x) zs[i] = zg[i];
   if (move == 1 && tid < D) zs[K * D + tid] = s_znew[tid];
   __syncthreads();
@@ -415,6 +419,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (tid < 4) s_minv[tid] = (CT)kp.minv[4 * prob + tid];
   const CT* minv = s_minv;
   const double* zg = kp.z + gi * (int64_t)kd;
+  if (PREC == MIXED) fill_exp_table(sm.exptab);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
   block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);

@@ -358,6 +358,7 @@ struct EvalSmem {
   double* red;    // [32*4] reduction scratch
   double* scal;   // [4]: logp, ll_old, ll_new, component*samples computed
   const double* tw;  // LINAMP fixed (t0, w) [kmax][2] (global)
+  float2* exptab;    // mixed path: 2^(j/64), j < 64, as double-float (filled per block)
   // mixed path: FP32 views of the same storage
   __device__ float* fth() const { return reinterpret_cast<float*>(th); }
   __device__ float* fdth() const { return reinterpret_cast<float*>(dth); }
@@ -398,6 +399,100 @@ __device__ __forceinline__ DF warp_sum_df(DF v) {
 }
 
 __device__ __forceinline__ double df_to_double(DF v) { return (double)v.hi + (double)v.lo; }
+
+__device__ __forceinline__ DF df_from(float2 v) { return DF{v.x, v.y}; }
+
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+// 1 / a (a > 0): FP32 reciprocal refined by one Newton step in double-float
+__device__ __forceinline__ DF df_recip(DF a) {
+  const float q = __frcp_rn(a.hi);
+  // residual 1 - a q, exact for the hi part by FMA
+  const float r = __fsub_rn(__fmaf_rn(-a.hi, q, 1.0f), __fmul_rn(a.lo, q));
+  return quick_two_sum(q, __fmul_rn(q, r));
+}
+
+// 2^(j/64), j < 64, as double-float, into shared memory (threads 0..63 of the block)
+__device__ __forceinline__ void fill_exp_table(float2* tab) {
+  if (threadIdx.x < 64) {
+    const double v = exp2((double)threadIdx.x / 64.0);
+    const float hi = (float)v;
+    tab[threadIdx.x] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+// e^x as double-float for x in [-80, 80], FP32 arithmetic only (table-driven method of
+// Tang, ACM TOMS 15(2), 1989): x = n ln2/64 + r with n integer and |r| <= ln2/128,
+// e^x = 2^(n div 64) 2^((n mod 64)/64) e^r, e^r from its Taylor series to r^5.
+// Relative error ~1e-12.
+__device__ __forceinline__ DF df_exp(DF x, const float2* tab) {
+  if (x.hi < -80.0f) x = DF{-80.0f, 0.0f};     // e^-80 ~ 1.8e-35: below every use here
+  if (x.hi > 80.0f) x = DF{80.0f, 0.0f};
+  const float n = rintf(__fmul_rn(x.hi, 92.3324813842773438f));   // 64 / ln 2 (FP32)
+  // ln2/64 = L1 + L2 + L3, L1 with 11 significant bits so n * L1 is exact for |n| < 2^13
+  constexpr float L1 = 0.01082611083984375f;               // 0x1.62cp-7
+  constexpr float L2 = 4.313856607041089e-06f;
+  constexpr float L3 = -2.0164562565278682e-13f;
+  const float r1 = __fmaf_rn(-n, L1, x.hi);                // exact
+  const float p2 = __fmul_rn(n, L2);
+  DF r = two_sum(r1, -p2);
+  r.lo = __fadd_rn(r.lo, __fsub_rn(x.lo, __fmaf_rn(n, L2, -p2)));
+  r.lo = __fsub_rn(r.lo, __fmul_rn(n, L3));
+  r = quick_two_sum(r.hi, r.lo);
+  const float rh = r.hi;
+  // e^r - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r / 120)))
+  float q = __fmaf_rn(rh, 1.0f / 120.0f, 1.0f / 24.0f);
+  q = __fmaf_rn(rh, q, 1.0f / 6.0f);
+  q = __fmaf_rn(rh, q, 0.5f);
+  q = __fmul_rn(__fmul_rn(rh, rh), q);
+  DF em1 = df_add(r, DF{q, 0.0f});
+  DF er = df_add(DF{1.0f, 0.0f}, em1);
+  const int ni = (int)n;
+  const int j = ni & 63;
+  const int k = (ni - j) / 64;   // floor division (ni - j is a multiple of 64)
+  DF v = df_mul(df_from(tab[j]), er);
+  return DF{ldexpf(v.hi, k), ldexpf(v.lo, k)};
+}
+
+// theta of parameter d from an FP64 coordinate, as double-float (uniform or log-uniform
+// map), with s(z) and 1 - s(z) both from e^{-|z|}; also returns dtheta/dz in FP32
+__device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, double z, const float2* tab,
+                                       float& dth) {
+  const float zh = (float)z;
+  const DF az = zh >= 0.f ? DF{zh, (float)(z - (double)zh)} : DF{-zh, -(float)(z - (double)zh)};
+  const DF e = df_exp(df_neg(az), tab);              // e^{-|z|}
+  const DF q = df_recip(df_add(DF{1.0f, 0.0f}, e));  // 1 / (1 + e)
+  const DF eq = df_mul(e, q);
+  const DF s = z >= 0.0 ? q : eq;                    // s(z)
+  const float ds = __fmul_rn(q.hi, eq.hi);           // s (1 - s)
+  const DF span = df_from(pb.f_span[d]);
+  DF th = df_add(df_from(pb.f_off[d]), df_mul(span, s));
+  if (pb.logmask & (1u << d)) {
+    th = df_exp(th, tab);
+    dth = th.hi * span.hi * ds;
+  } else {
+    dth = span.hi * ds;
+  }
+  return th;
+}
 
 template <int MODEL>
 __device__ __forceinline__ void finish_component(int prec, const double* th, const double* S,
@@ -533,6 +628,25 @@ __device__ __forceinline__ void pulse_prep32(float A, double t0, double w, const
 // (sample indices as FP32, exact below 2^24; converted once per segment)
 __device__ __forceinline__ bool outside_support(const float* cf, float first, float last) {
   return last < cf[9] || first > cf[10];
+}
+
+__device__ __forceinline__ void pulse_prep_df(float A, DF t0, float w, const ProbDev& pb,
+                                              float* cf) {
+  const float kap = __fdiv_rn(0.849321800288019f, w);    // sqrt(log2(e)/2) / w
+  const DF a0 = df_mul_f(df_add(df_from(pb.f_to), df_neg(t0)), kap);
+  const DF del = df_mul_f(df_from(pb.f_dt), kap);
+  cf[0] = A;
+  cf[1] = a0.hi;
+  cf[2] = a0.lo;
+  cf[3] = del.hi;
+  cf[4] = del.lo;
+  cf[5] = exp2f(-2.f * del.hi * del.hi);
+  cf[6] = 2.f * del.hi;
+  cf[7] = del.hi * del.hi;
+  cf[8] = del.hi > 0.5f ? 1.0f : 0.0f;
+  const float idel = __frcp_rn(del.hi);
+  cf[9] = fmaxf(floorf((-7.0f - a0.hi) * idel) - 2.0f, -1.0e30f);
+  cf[10] = fminf(ceilf((7.0f - a0.hi) * idel) + 2.0f, 1.0e30f);
 }
 
 __device__ __forceinline__ void sin_prep32(float A, double f, float fd, float p0,
@@ -912,13 +1026,14 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       dth[k * D + 1] = (float)d1;
       sin_prep32(t[0], f, t[2], t[3], pb, cf);
     } else if (MODEL == PULSE) {
-      double d1, d2;
-      const double t0 = theta64(pb, 1, zk[1], d1);
-      const double w = theta64(pb, 2, zk[2], d2);
-      th[k * D + 2] = (float)w;
-      dth[k * D + 1] = (float)d1;
-      dth[k * D + 2] = (float)d2;
-      pulse_prep32(t[0], t0, w, pb, cf);
+      // centre and width to ~1e-12 relative in double-float (FP32 pipe, no FP64)
+      float d1, d2;
+      const DF t0 = theta_df(pb, 1, zk[1], sm.exptab, d1);
+      const DF w = theta_df(pb, 2, zk[2], sm.exptab, d2);
+      th[k * D + 2] = w.hi;
+      dth[k * D + 1] = d1;
+      dth[k * D + 2] = d2;
+      pulse_prep_df(t[0], t0, w.hi, pb, cf);
     } else {
       pulse_prep32(t[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
     }
