@@ -34,6 +34,10 @@ UNIT = "cs-evals/s"
 OPS_PER_CS = {0: 9.0, 1: 14.0}   # algorithmic FP32 lane-ops per component*sample (fwd+adj)
 FP32_LANES_PER_SM = 128
 N_SM = 148
+# DRAM bytes (read + write) per particle of one NUTS launch, from an ncu capture of the
+# same kernel on a 1024-particle launch of this workload (641 KB / 1024 particles);
+# traffic scales with the particle count (z rows in and out; the samples stay in L2)
+NUTS_DRAM_BYTES_PER_PARTICLE = 626.0
 
 
 def _args():
@@ -240,7 +244,9 @@ def run_gpu(a):
     peak = FP32_LANES_PER_SM * N_SM * mhz * 1e6 / 1e12
     roof = {"kernel": "k_nuts<PULSE,MIXED,32>", "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "Tops/s (FP32 lane-ops, FMA=1)", "frac": achieved / peak,
-            "traffic": None, "launches": n_nuts, "ms_per_launch": per_launch_ms,
+            "traffic": NUTS_DRAM_BYTES_PER_PARTICLE * a.particles,
+            "traffic_note": "ncu dram__bytes_read+write of a 1024-particle launch, scaled per particle",
+            "launches": n_nuts, "ms_per_launch": per_launch_ms,
             "share_of_step": ms_nuts / ms, "peak_basis": f"128 FP32 lanes x 148 SMs x {mhz:.0f} MHz"
                                                          " (median SM clock during the timed region)",
             "ops_per_cs": OPS_PER_CS[wl.model],
