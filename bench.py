@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--samples", type=int, default=16384)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=500,
                     help="nvidia-smi sampling interval (200 ms polling slows kernels on this part)")
     ap.add_argument("--clock-fields", default="full", choices=["full", "clocks"])
@@ -172,6 +173,109 @@ class ClockSampler:
                           and "Not" not in r[5 + j]})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _events_ms(stream, fn):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_extras(stream):
+    """Secondary measurements: mixed vs FP64 logL+grad throughput, SMC wall time at equal
+    error against the oracle reference, and the 64-band batched workload."""
+    import json as _json
+
+    import torch
+
+    from paper_2609_17674_b300 import autotune, capi, sampler, synth
+
+    out = {}
+    # (1) batched logL+grad kernel, pulse N=16384, K_max=40, P=8192, prior population
+    wl = synth.config2()
+    z, K = synth.prior_population(wl, 1)
+    zd, Kd = torch.as_tensor(z, device="cuda"), torch.as_tensor(K, device="cuda")
+    beta = torch.tensor([0.5], dtype=torch.float64, device="cuda")
+    cs = float(K.sum()) * wl.problems[0].n
+    thr = {}
+    for name, prec, win in (("mixed", capi.MIXED, 1), ("mixed_no_window", capi.MIXED, 0),
+                            ("fp64", capi.FP64, 0)):
+        ctx = sampler.open_context(wl, prec, stream=stream, pulse_window=win)
+        ctx.set_population(zd, Kd, beta=[0.5])
+        g = torch.empty_like(zd)
+        with torch.cuda.stream(stream):
+            ctx.eval(zd, Kd, beta, grad=True, g=g)
+        ms = min(_events_ms(stream, lambda: ctx.eval(zd, Kd, beta, grad=True, g=g))
+                 for _ in range(2 if prec == capi.FP64 else 5))
+        thr[name] = cs / (ms * 1e-3)
+        ctx.close()
+    out["logl_grad_kernel"] = {"workload": wl.name + " (prior population)", "unit": UNIT,
+                               **thr, "mixed_over_fp64": thr["mixed"] / thr["fp64"],
+                               "mixed_no_window_over_fp64": thr["mixed_no_window"] / thr["fp64"]}
+    # (2) full SMC, N=1024 pulses, FP64 vs mixed, against the 20-run oracle reference
+    gold = os.path.join(ROOT, "tests", "golden", "smc_config1_oracle.json")
+    if os.path.exists(gold):
+        runs = _json.load(open(gold))["runs"]
+        gh = np.array([r["hist"] for r in runs])
+        gz = np.array([r["logz"] for r in runs])
+        res = {}
+        for name, prec in (("fp64", capi.FP64), ("mixed", capi.MIXED)):
+            hs, zs, ts = [], [], []
+            for seed in range(4):
+                w1 = synth.config1()
+                w1.seed = seed
+                ctx = sampler.open_context(w1, prec, stream=stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                o = sampler.run_smc(ctx, max_stages=400)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                _, Kp, _, _ = ctx.get_population()
+                hs.append(np.bincount(Kp.cpu().numpy(), minlength=w1.kmax + 1) / w1.P)
+                zs.append(o["logz"][-1][0])
+                ctx.close()
+            hs, zs = np.array(hs), np.array(zs)
+            se_h = np.sqrt(hs.var(0, ddof=1) / len(hs) + gh.var(0, ddof=1) / len(gh))
+            se_z = math.sqrt(zs.var(ddof=1) / len(zs) + gz.var(ddof=1) / len(gz))
+            res[name] = {"wall_s_per_run": float(np.median(ts)), "logz": float(zs.mean()),
+                         "within_3se": bool(np.all(np.abs(hs.mean(0) - gh.mean(0)) <= 3 * se_h + 0.01)
+                                            and abs(zs.mean() - gz.mean()) <= 3 * se_z + 0.02)}
+        res["oracle_logz"] = float(gz.mean())
+        res["fp64_over_mixed_wall"] = res["fp64"]["wall_s_per_run"] / res["mixed"]["wall_s_per_run"]
+        out["smc_equal_error_pulse_n1024_p512"] = res
+    # (3) 64 independent GB bands (N_b 2^14..2^18, P=2048 each) in one launch
+    w5 = synth.config5()
+    nb = len(w5.problems)
+    best = autotune.tune(w5, capi.MIXED, nuts=False)
+    ctx = sampler.open_context(w5, capi.MIXED, stream=stream, threads=best["threads"],
+                               samples_per_thread=best["samples_per_thread"])
+    zs, Ks = [], []
+    for b in range(nb):
+        zb, Kb = synth.prior_population(w5, 100 + b, w5.P)
+        zs.append(zb)
+        Ks.append(Kb)
+    z5, K5 = np.concatenate(zs), np.concatenate(Ks)
+    zd5, Kd5 = torch.as_tensor(z5, device="cuda"), torch.as_tensor(K5, device="cuda")
+    ctx.set_population(zd5, Kd5, beta=[1e-3] * nb)
+    b5 = torch.full((nb,), 0.5, dtype=torch.float64, device="cuda")
+    g5 = torch.empty_like(zd5)
+    cs5 = float(sum(K5[b * w5.P:(b + 1) * w5.P].sum() * w5.problems[b].n for b in range(nb)))
+    ms5 = min(_events_ms(stream, lambda: ctx.eval(zd5, Kd5, b5, grad=True, g=g5)) for _ in range(3))
+    ctx.update_metric()
+    ctx.counters(reset=True)
+    msn = _events_ms(stream, lambda: ctx.nuts_move(0, 0))
+    (_, cn, _, _), _ = ctx.counters(reset=True)
+    out["gb_bands_64x2048"] = {"unit": UNIT, "launch_shape": best,
+                               "logl_grad_kernel": cs5 / (ms5 * 1e-3),
+                               "nuts_transition": cn / (msn * 1e-3), "nuts_ms": msn}
+    ctx.close()
+    return out
 
 
 def run_gpu(a):
@@ -313,6 +417,7 @@ def run_gpu(a):
                "sample": f"{cores} particles of the same workload (one per core, {cores} "
                          "processes): logL+grad, metric, one RJ move and one NUTS transition "
                          f"each; {busy:.1f} s"}
+    extras = None if a.no_extras else measure_extras(stream)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
@@ -329,7 +434,7 @@ def run_gpu(a):
                    "stages": [stage - a.steps - (max(2, a.steps // 2) if e2e else 0), stage],
                    "beta_end": betas[-1]},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk,
+        "clocks": clk, "extras": extras,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:
