@@ -58,10 +58,9 @@ def _args():
 
 
 def workload(rank: int, P: int, n: int):
-    from paper_2609_17674_b300 import synth
+    from paper_2609_17674_b300 import dist as tdist, synth
 
-    wl = synth.config2(seed=1002 + 1000 * rank, P=P, n=n)
-    return wl
+    return synth.config2(seed=tdist.rank_seed(1002, rank), P=P, n=n)
 
 
 # ---------------------------------------------------------------------------
@@ -335,8 +334,10 @@ def run_gpu(a):
     (cs_eval, cs_nuts, cc_eval, cc_nuts), launches = ctx.counters(reset=True)
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    ms_max = reduce(ms, dist.ReduceOp.MAX if dist else None)
-    cs_total = reduce(float(cs_eval + cs_nuts), dist.ReduceOp.SUM if dist else None)
+    from paper_2609_17674_b300 import dist as tdist
+
+    ms_max, cs_total = tdist.reduce_measurement(ms, float(cs_eval + cs_nuts),
+                                                device=torch.device("cuda", local))
     value = cs_total / (ms_max * 1e-3)
 
     # roofline of the dominant kernel (NUTS transition), ALU bound (FP32 pipe)

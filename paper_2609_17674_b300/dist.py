@@ -1,0 +1,32 @@
+"""Multi-GPU bookkeeping for weak scaling (one process per GPU, no data-path collective).
+
+Independent problems are sharded across ranks; only the measurement is reduced:
+the elapsed time as the maximum over ranks and the evaluation counts as their sum.
+"""
+from __future__ import annotations
+
+
+def shard(n_units: int, world: int, rank: int):
+    """Contiguous block of unit indices for rank (sizes differ by at most one)."""
+    base, extra = divmod(n_units, world)
+    start = rank * base + min(rank, extra)
+    return list(range(start, start + base + (1 if rank < extra else 0)))
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Data and Philox seed of a rank's independent problem."""
+    return seed + 1000 * rank
+
+
+def reduce_measurement(ms: float, cs: float, group=None, device=None):
+    """(max elapsed ms over ranks, total component*samples over ranks)."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized():
+        return ms, cs
+    t = torch.tensor([ms, -cs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    s = torch.tensor([cs], dtype=torch.float64, device=device)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
+    return float(t[0].item()), float(s[0].item())

@@ -355,3 +355,76 @@ def test_pulse_window_matches_full_evaluation():
     np.testing.assert_allclose(l1, l0, rtol=1e-6)
     res = oracle.Oracle(wl).logl_grad(z[:8], K[:8], 0.3)
     assert np.all(np.abs(g1[:8] - g0[:8]) <= 1e-5 * res["gscale"] + 1e-300)
+
+
+def test_mixture_schedule_stage_matches_oracle_fp64():
+    """The paper's kernel mixture (p_NUTS, p_birth, p_death = 0.6, 0.2, 0.2 per round)."""
+    wl = synth.config1()
+    wl.P = 128
+    wl.n_mut = 3
+    wl.schedule = synth.SCHED_MIXTURE
+    wl.p_nuts, wl.p_birth, wl.p_death = 0.6, 0.2, 0.2
+    ctx = sampler.open_context(wl, capi.FP64)
+    ctx.init_population()
+    b, lz, _ = ctx.run_stage(0, use_graph=False)
+    z, K, _, _ = ctx.get_population()
+    res = oracle.Oracle(wl).smc_run(128, max_stages=1)
+    assert b[0] == pytest.approx(res["beta"][0], abs=1e-13)
+    Kg = K.cpu().numpy()
+    assert np.mean(Kg == res["K"]) > 0.95
+    same = Kg == res["K"]
+    close = np.all(np.isclose(z.cpu().numpy(), res["z"], rtol=1e-8, atol=1e-8), axis=(1, 2))
+    assert np.mean(close[same]) > 0.9
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_linear_gaussian_evidence_on_gpu(prec):
+    """SMC log Z and posterior mean against the closed form of the linear-Gaussian model."""
+    lz, mu = [], []
+    for seed in range(8):
+        wl = synth.linamp_workload(n=256, k=3, P=1024, seed=31)
+        wl.seed = 200 + seed
+        ctx = sampler.open_context(wl, prec)
+        out = sampler.run_smc(ctx, max_stages=200)
+        z, _, _, _ = ctx.get_population()
+        lz.append(out["logz"][-1][0])
+        mu.append(z.cpu().numpy().reshape(-1, 3).mean(0))
+        ctx.close()
+    pr = wl.problems[0]
+    t = np.arange(pr.n) / pr.n
+    G = np.exp(-((t[:, None] - wl.fixed_tw[None, :, 0]) ** 2) / (2 * wl.fixed_tw[None, :, 1] ** 2))
+    s2 = pr.sigma ** 2
+    S = s2 * np.eye(pr.n) + wl.amp_sd ** 2 * G @ G.T
+    res_ = pr.d - G @ np.full(3, wl.amp_mean)
+    logz_full = -0.5 * res_ @ np.linalg.solve(S, res_) - 0.5 * np.linalg.slogdet(S)[1] \
+        - 0.5 * pr.n * math.log(2 * math.pi)
+    logz_exact = logz_full + 0.5 * pr.n * math.log(2 * math.pi * s2)
+    prec_m = np.eye(3) / wl.amp_sd ** 2 + G.T @ G / s2
+    cov = np.linalg.inv(prec_m)
+    mean = cov @ (np.full(3, wl.amp_mean) / wl.amp_sd ** 2 + G.T @ pr.d / s2)
+    lz, mu = np.array(lz), np.array(mu)
+    se = max(lz.std(ddof=1) / math.sqrt(len(lz)), 0.01)
+    assert abs(lz.mean() - logz_exact) < 3 * se + 0.02, (lz.mean(), logz_exact, se)
+    sem = np.sqrt(np.diag(cov) / 1024 + mu.var(0, ddof=1) / len(mu))
+    assert np.all(np.abs(mu.mean(0) - mean) < 4 * sem)
+
+
+def test_state_errors_and_constant_ell():
+    t = torch()
+    wl = synth.config1()
+    cfg = sampler.make_config(wl, capi.FP64)
+    ctx = capi.Context(cfg, [1024])
+    with pytest.raises(capi.TsmcError, match="error -6"):     # no data yet
+        ctx.init_population()
+    with pytest.raises(capi.TsmcError, match="error -6"):     # no population yet
+        ctx.nuts_move(0, 0)
+    # all particles with K = 0 have the same likelihood: ESS = P at any beta -> beta' = 1
+    ctx2 = sampler.open_context(wl, capi.FP64)
+    ctx2.set_population(dev_tensor(np.zeros((512, 10, 3))), dev_tensor(np.zeros(512, np.int32)),
+                        beta=[0.0])
+    b, lz, e = ctx2.temper_reweight_resample(0)
+    d = wl.problems[0].d
+    assert b[0] == 1.0 and e[0] == pytest.approx(512.0)
+    assert lz[0] == pytest.approx(-0.5 * np.sum(d * d) / 0.01, rel=1e-12)
+    anc = ctx2.get_ancestors().cpu().numpy()
+    assert np.array_equal(anc, np.arange(512))
