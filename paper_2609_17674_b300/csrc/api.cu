@@ -185,6 +185,8 @@ SmemPlan smem_plan(Ctx* c, bool fisher, int depth) {
   sp.nw = c->T / 32;
   sp.depth = depth;
   sp.fisher = fisher;
+  const int span = 32 * c->R;
+  sp.nwr = c->cfg.precision == TSMC_MIXED ? (int)((c->nmax + span - 1) / span) : 0;
   return sp;
 }
 

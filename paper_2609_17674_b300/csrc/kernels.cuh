@@ -34,9 +34,10 @@ struct SmemPlan {
   int nw;          // warps per block
   int depth;       // NUTS checkpoint levels (0 for non-NUTS kernels)
   bool fisher;
+  int nwr;         // warp ranges of the longest problem (active-component masks)
   __host__ __device__ size_t eval_bytes() const {
     return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4 + 64) +
-           sizeof(float) * (size_t)kd * NCF + 16;
+           sizeof(float) * (size_t)kd * NCF + sizeof(uint32_t) * 2 * (size_t)nwr + 32;
   }
   __host__ __device__ size_t nuts_bytes() const {
     return sizeof(double) * (size_t)kd * (13 + 2 * (size_t)(depth + 1));   // 8-byte slots
@@ -65,7 +66,8 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
   sm.exptab = reinterpret_cast<float2*>(d); d += 64;
   if (reinterpret_cast<uintptr_t>(d) & 8) d += 1;   // float4 loads of the constants
   sm.cf = reinterpret_cast<float*>(d);
-  p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kd * NCF);
+  sm.wmask = reinterpret_cast<uint32_t*>(sm.cf + (size_t)sp.kd * NCF);
+  p = reinterpret_cast<char*>(sm.wmask + 2 * (size_t)sp.nwr);
   // keep 8-byte alignment for what follows
   p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
   sm.tw = tw;
@@ -369,6 +371,14 @@ __device__ __forceinline__ CT warp_dot_minv(const CT* a, const CT* b, const CT* 
   return warp_sum(s);
 }
 
+// One out-of-line copy of the block evaluation for the NUTS kernel, which evaluates at
+// two sites (initial point, every leaf): a single copy keeps the kernel's code small.
+template <int MODEL, int PREC, int R>
+__device__ __noinline__ void nuts_eval(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
+                                       const double* z, EvalSmem& sm, double* g) {
+  block_eval<MODEL, PREC, R, true, false>(pb, pa, K, beta, z, sm, g, nullptr);
+}
+
 template <int MODEL, int PREC, int R>
 __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
   using CT = typename std::conditional<PREC == MIXED, float, double>::type;
@@ -422,7 +432,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (PREC == MIXED) fill_exp_table(sm.exptab);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
-  block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+  nuts_eval<MODEL, PREC, R>(pb, kp.pa, K, beta, z1, sm, g1);
   double cs_done = sm.scal[3];   // component*samples computed (thread 0)
   // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
   // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
@@ -482,7 +492,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         }
       }
       __syncthreads();
-      block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+      nuts_eval<MODEL, PREC, R>(pb, kp.pa, K, beta, z1, sm, g1);
       cs_done += sm.scal[3];
       if (warp == 0) {
         CT kin = 0;

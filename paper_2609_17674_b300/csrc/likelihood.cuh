@@ -197,6 +197,46 @@ __device__ __forceinline__ void mixed_vals(const float* cf, float m, float (&h)[
   }
 }
 
+// r_j -= h(t_{m+j}) for one component on the thread's R samples (fused multiply-adds)
+template <int MODEL, int R>
+__device__ __forceinline__ void mixed_sub(const float* cf, float m, float (&r)[R]) {
+  if (MODEL == SINUSOID) {
+    float c, s;
+    sin_anchor(cf, m, c, s);
+    const float nA = -cf[0], rc = cf[5], rs = cf[6];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      r[j] = __fmaf_rn(nA, c, r[j]);
+      const float c2 = __fmaf_rn(c, rc, -s * rs);
+      s = __fmaf_rn(s, rc, c * rs);
+      c = c2;
+    }
+  } else {
+    const float nA = -cf[0];
+    const float v00 = dd_axpy(cf[1], cf[2], cf[3], cf[4], m);
+    if (cf[8] != 0.0f) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const float v = __fmaf_rn((float)j, cf[3], v00);
+        r[j] = __fmaf_rn(nA, ex2a(-v * v), r[j]);
+      }
+    } else {
+#pragma unroll
+      for (int c8 = 0; c8 < R / 8; ++c8) {
+        const float v0 = __fmaf_rn((float)(8 * c8), cf[3], v00);
+        float g = ex2a(-v0 * v0);
+        float q = ex2a(fminf(-__fmaf_rn(v0, cf[6], cf[7]), 64.0f));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          r[8 * c8 + j] = __fmaf_rn(nA, g, r[8 * c8 + j]);
+          g *= q;
+          q *= cf[5];
+        }
+      }
+    }
+  }
+}
+
 // adjoint partial sums of one component over the thread's samples (rc = c_n r_n / sigma^2)
 //   pulse:    s0 = sum rc g, s1 = sum rc g v, s2 = sum rc g v^2
 //   sinusoid: s0 = sum rc cos, s1 = sum rc sin, s2 = sum rc sin n, s3 = sum rc sin n^2
@@ -359,6 +399,7 @@ struct EvalSmem {
   double* scal;   // [4]: logp, ll_old, ll_new, component*samples computed
   const double* tw;  // LINAMP fixed (t0, w) [kmax][2] (global)
   float2* exptab;    // mixed path: 2^(j/64), j < 64, as double-float (filled per block)
+  uint32_t* wmask;   // mixed pulse path: [warp ranges][2] bits of the components active there
   // mixed path: FP32 views of the same storage
   __device__ float* fth() const { return reinterpret_cast<float*>(th); }
   __device__ float* fdth() const { return reinterpret_cast<float*>(dth); }
@@ -677,52 +718,14 @@ __device__ __forceinline__ void sin_prep32(float A, double f, float fd, float p0
 // ---------------------------------------------------------------------------
 template <int MODEL, int PREC>
 __device__ double eval_setup_any(const ProbDev& pb, const PriorArgs& pa, int K, const double* z,
-                             EvalSmem& sm) {
+                                 EvalSmem& sm) {
   constexpr int D = model_d<MODEL>();
   double lp_sum = 0.0;
-  if (PREC == FP64) {
-    for (int i = threadIdx.x; i < K * D; i += blockDim.x) {
-      double th, dth, lp, pg, pc;
-      coord(pb, pa, i % D, z[i], th, dth, lp, pg, pc);
-      sm.th[i] = th; sm.dth[i] = dth; sm.pg[i] = pg; sm.pc[i] = pc;
-      lp_sum += lp;
-    }
-    __syncthreads();
-    return lp_sum;
-  }
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const double* zk = z + k * D;
-    float lp = 0.f, th[4];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const Coord32 c = coord32(pb, pa, d, (float)zk[d]);
-      th[d] = c.th;
-      sm.th[k * D + d] = (double)c.th;
-      sm.dth[k * D + d] = (double)c.dth;
-      sm.pg[k * D + d] = (double)c.pg;
-      sm.pc[k * D + d] = (double)c.pc;
-      lp += c.lp;
-    }
-    float* cf = sm.cf + k * NCF;
-    if (MODEL == SINUSOID) {
-      double dth;
-      const double f = theta64(pb, 1, zk[1], dth);
-      sm.th[k * D + 1] = f;
-      sm.dth[k * D + 1] = dth;
-      sin_prep32(th[0], f, th[2], th[3], pb, cf);
-    } else if (MODEL == PULSE) {
-      double dt0, dw;
-      const double t0 = theta64(pb, 1, zk[1], dt0);
-      const double w = theta64(pb, 2, zk[2], dw);
-      sm.th[k * D + 1] = t0;
-      sm.dth[k * D + 1] = dt0;
-      sm.th[k * D + 2] = w;
-      sm.dth[k * D + 2] = dw;
-      pulse_prep32(th[0], t0, w, pb, cf);
-    } else {
-      pulse_prep32(th[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
-    }
-    lp_sum += (double)lp;
+  for (int i = threadIdx.x; i < K * D; i += blockDim.x) {
+    double th, dth, lp, pg, pc;
+    coord(pb, pa, i % D, z[i], th, dth, lp, pg, pc);
+    sm.th[i] = th; sm.dth[i] = dth; sm.pg[i] = pg; sm.pc[i] = pc;
+    lp_sum += lp;
   }
   __syncthreads();
   return lp_sum;
@@ -757,201 +760,97 @@ __device__ __forceinline__ void load_cf(const float* cf, float (&o)[NCF]) {
 // ---------------------------------------------------------------------------
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
 __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
-                           const double* z, EvalSmem& sm, double* grad_out, double* fis_out) {
+                                const double* z, EvalSmem& sm, double* grad_out,
+                                double* fis_out) {
   constexpr int D = model_d<MODEL>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nw = blockDim.x >> 5;
   const double lp_sum = eval_setup_any<MODEL, PREC>(pb, pa, K, z, sm);
 
   const int64_t N = pb.n, n1 = pb.n1;
-  double acc_old = 0.0, acc_new = 0.0;          // FP64 path
-  float eo_s = 0.f, eo_c = 0.f, en_s = 0.f, en_c = 0.f;   // mixed path energies
+  double acc_old = 0.0, acc_new = 0.0;
   // per-lane slot sums for components k = lane (slot 0) and lane + 32 (slot 1)
-  float gs[2][4], gc[2][4], fs[2][4], fc[2][4];
   double ga[2][4], fa[2][4];
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      gs[s][d] = gc[s][d] = fs[s][d] = fc[s][d] = 0.f;
-      ga[s][d] = fa[s][d] = 0.0;
-    }
-
-  const bool win = PREC == MIXED && MODEL != SINUSOID && pa.window;
+    for (int d = 0; d < 4; ++d) ga[q][d] = fa[q][d] = 0.0;
   double done = 0.0;   // component*samples computed by this thread
   const int64_t seg = (int64_t)blockDim.x * R;
   for (int64_t base = 0; base < N; base += seg) {
     const int64_t wfirst = base + (int64_t)warp * 32 * R;
     if (wfirst >= N) continue;  // whole warp past the end (warp-uniform)
-    const int64_t wlast = wfirst + 32 * R - 1;
     const int64_t m = base + (int64_t)tid * R;
     const double mine = (double)(m < N ? (m + R <= N ? R : N - m) : 0);
-
-    if (PREC == MIXED) {
-      const float beta_f = (float)beta, inv_s2_f = (float)pb.inv_s2;
-      float r[R];
-      if (m + R <= N) {
-        const float4* src = reinterpret_cast<const float4*>(pb.d32 + m);
+    double hs[R], r[R];
+    done += mine * K;
 #pragma unroll
-        for (int q = 0; q < R / 4; ++q) {
-          const float4 v = src[q];
-          r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
-        }
-      } else {
+    for (int j = 0; j < R; ++j) hs[j] = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double* th = sm.th + k * D;
+      const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
+      const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
 #pragma unroll
-        for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
-      }
-      const float mf = (float)m;
-      for (int k = 0; k < K; ++k) {
-        float cf[NCF], h[R];
-        load_cf(sm.cf + k * NCF, cf);
-        if (win && outside_support(cf, wfirst, wlast)) continue;
-        done += mine;
-        mixed_vals<MODEL, R>(cf, mf, h);
+      for (int j = 0; j < R; ++j)
+        hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), nullptr));
+    }
 #pragma unroll
-        for (int j = 0; j < R; ++j) r[j] -= h[j];
-      }
-      // residual energy and the adjoint weights rc = c_n r_n / sigma^2
-      float so = 0.f, sn = 0.f;
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int64_t n = m + j;
-        const bool valid = n < N, old = n < n1;
-        const float rr = valid ? r[j] : 0.0f;
-        const float e = rr * rr;
-        if (old) so += e; else sn += e;
-        r[j] = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
-      }
-      kahan_add(eo_s, eo_c, so);
-      kahan_add(en_s, en_c, sn);
-      if (GRAD) {
-        for (int k = 0; k < K; ++k) {
-          float cf[NCF], o[4];
-          load_cf(sm.cf + k * NCF, cf);
-          if (win && outside_support(cf, wfirst, wlast)) continue;
-          mixed_adj<MODEL, R>(cf, mf, r, o);
-#pragma unroll
-          for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
-          if (lane == (k & 31)) {
-            if (k < 32) {
-#pragma unroll
-              for (int d = 0; d < D; ++d) kahan_add(gs[0][d], gc[0][d], o[d]);
-            } else {
-#pragma unroll
-              for (int d = 0; d < D; ++d) kahan_add(gs[1][d], gc[1][d], o[d]);
-            }
-          }
-        }
-      }
-      if (FISHER) {
-        float cw[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int64_t n = m + j;
-          cw[j] = n < N ? (n < n1 ? inv_s2_f : beta_f * inv_s2_f) : 0.0f;
-        }
-        for (int k = 0; k < K; ++k) {
-          float cf[NCF], o[4];
-          load_cf(sm.cf + k * NCF, cf);
-          if (win && outside_support(cf, wfirst, wlast)) continue;
-          mixed_fis<MODEL, R>(cf, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
-#pragma unroll
-          for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
-          if (lane == (k & 31)) {
-            if (k < 32) {
-#pragma unroll
-              for (int d = 0; d < D; ++d) kahan_add(fs[0][d], fc[0][d], o[d]);
-            } else {
-#pragma unroll
-              for (int d = 0; d < D; ++d) kahan_add(fs[1][d], fc[1][d], o[d]);
-            }
-          }
-        }
-      }
-    } else {
-      // ---------------- FP64 path ----------------
-      double hs[R], r[R];
-      done += mine * K;
-#pragma unroll
-      for (int j = 0; j < R; ++j) hs[j] = 0.0;
+    for (int j = 0; j < R; ++j) {
+      const int64_t n = m + j;
+      const bool valid = n < N, old = n < n1;
+      const double rr = valid ? __dadd_rn(pb.d64[valid ? n : 0], -hs[j]) : 0.0;
+      const double e = __dmul_rn(rr, rr);
+      if (old) acc_old += e; else acc_new += e;
+      r[j] = __dmul_rn(old ? 1.0 : beta, rr);   // c_n r_n (1/sigma^2 applied at the end)
+    }
+    if (GRAD || FISHER) {
       for (int k = 0; k < K; ++k) {
         const double* th = sm.th + k * D;
         const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
         const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
+        double o[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-          hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), nullptr));
-      }
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int64_t n = m + j;
-        const bool valid = n < N, old = n < n1;
-        const double rr = valid ? __dadd_rn(pb.d64[valid ? n : 0], -hs[j]) : 0.0;
-        const double e = __dmul_rn(rr, rr);
-        if (old) acc_old += e; else acc_new += e;
-        r[j] = __dmul_rn(old ? 1.0 : beta, rr);   // c_n r_n (1/sigma^2 applied at the end)
-      }
-      if (GRAD || FISHER) {
-        for (int k = 0; k < K; ++k) {
-          const double* th = sm.th + k * D;
-          const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
-          const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
-          double o[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            double dh[4];
-            fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), dh);
-            const int64_t n = m + j;
-            const double cn = n < N ? (n < n1 ? 1.0 : beta) : 0.0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              o[d] += __dmul_rn(r[j], dh[d]);
-              if (FISHER) f[d] += cn * dh[d] * dh[d];
-            }
-          }
+        for (int j = 0; j < R; ++j) {
+          double dh[4];
+          fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), dh);
+          const int64_t n = m + j;
+          const double cn = n < N ? (n < n1 ? 1.0 : beta) : 0.0;
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            if (GRAD) o[d] = warp_sum(o[d]);
-            if (FISHER) f[d] = warp_sum(f[d]);
+            o[d] += __dmul_rn(r[j], dh[d]);
+            if (FISHER) f[d] += cn * dh[d] * dh[d];
           }
-          if (lane == (k & 31)) {
-            const int s = k < 32 ? 0 : 1;
+        }
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-              if (s == 0) { ga[0][d] += o[d]; fa[0][d] += f[d]; }
-              else { ga[1][d] += o[d]; fa[1][d] += f[d]; }
-            }
+        for (int d = 0; d < D; ++d) {
+          if (GRAD) o[d] = warp_sum(o[d]);
+          if (FISHER) f[d] = warp_sum(f[d]);
+        }
+        if (lane == (k & 31)) {
+          const int q = k < 32 ? 0 : 1;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            if (q == 0) { ga[0][d] += o[d]; fa[0][d] += f[d]; }
+            else { ga[1][d] += o[d]; fa[1][d] += f[d]; }
           }
         }
       }
     }
-  }
-  if (PREC == MIXED) {
-    acc_old = (double)eo_s - (double)eo_c;
-    acc_new = (double)en_s - (double)en_c;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        ga[s][d] = (double)gs[s][d] - (double)gc[s][d];
-        fa[s][d] = (double)fs[s][d] - (double)fc[s][d];
-      }
   }
 
   // ---- gradient / Gauss-Newton assembly: per-warp slots -> shared -> components ----
   if (GRAD || FISHER) {
     const int KDm = K * D;
     for (int k = lane; k < K; k += 32) {
-      const int s = k < 32 ? 0 : 1;
+      const int q = k < 32 ? 0 : 1;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        if (GRAD) sm.wacc[warp * KDm + k * D + d] = s == 0 ? ga[0][d] : ga[1][d];
-        if (FISHER) sm.wfis[warp * KDm + k * D + d] = s == 0 ? fa[0][d] : fa[1][d];
+        if (GRAD) sm.wacc[warp * KDm + k * D + d] = q == 0 ? ga[0][d] : ga[1][d];
+        if (FISHER) sm.wfis[warp * KDm + k * D + d] = q == 0 ? fa[0][d] : fa[1][d];
       }
     }
-    // warps that skipped every segment still hold zeros: they wrote them above
     __syncthreads();
-    const double is2 = PREC == FP64 ? pb.inv_s2 : 1.0;
+    const double is2 = pb.inv_s2;
     for (int k = tid; k < K; k += blockDim.x) {
       double S[4] = {0, 0, 0, 0}, F[4] = {0, 0, 0, 0}, g[4], f[4];
       for (int w = 0; w < nw; ++w) {
@@ -992,18 +891,24 @@ __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, d
   __syncthreads();
 }
 
-
 // ---------------------------------------------------------------------------
 // Mixed path: setup, evaluation and reductions in FP32 (double-float where a
 // total needs more than 24 bits); FP64 only for the centre/width/frequency maps,
 // the template anchors and the final scalars of thread 0.
 // ---------------------------------------------------------------------------
-template <int MODEL>
+template <int MODEL, int R>
 __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const double* z,
                                   EvalSmem& sm) {
   constexpr int D = model_d<MODEL>();
   float lp = 0.f;
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
+  const bool win = MODEL != SINUSOID && pa.window;
+  const int span = 32 * R;                      // samples per warp range
+  const int nwr = ((int)pb.n + span - 1) / span;
+  if (win) {
+    for (int i = threadIdx.x; i < 2 * nwr; i += blockDim.x) sm.wmask[i] = 0u;
+    __syncthreads();
+  }
   // one thread per component, packed into as few warps as possible: an FP64 warp
   // instruction costs the same whether 1 or 32 lanes are active
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -1037,6 +942,13 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
     } else {
       pulse_prep32(t[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
     }
+    if (win) {   // mark the warp ranges that intersect the component's support
+      const float lo = fmaxf(cf[9], 0.0f), hi = fminf(cf[10], (float)(pb.n - 1));
+      if (lo <= hi) {
+        const int r0 = (int)lo / span, r1 = min((int)hi / span, nwr - 1);
+        for (int q = r0; q <= r1; ++q) atomicOr(&sm.wmask[2 * q + (k >> 5)], 1u << (k & 31));
+      }
+    }
   }
   __syncthreads();
   return lp;
@@ -1048,7 +960,7 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
   constexpr int D = model_d<MODEL>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nw = blockDim.x >> 5;
-  const float lp_t = eval_setup_mixed<MODEL>(pb, pa, K, z, sm);
+  const float lp_t = eval_setup_mixed<MODEL, R>(pb, pa, K, z, sm);
 
   // sample indices fit 32 bits (capacity < 2^24): no 64-bit integer work or
   // 64-bit conversions (which issue on the FP64 pipe) inside the sample loop
@@ -1067,7 +979,6 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
   for (int base = 0; base < N; base += seg) {
     const int wfirst = base + warp * 32 * R;
     if (wfirst >= N) continue;  // whole warp past the end (warp-uniform)
-    const float wf = (float)wfirst, wl = (float)(wfirst + 32 * R - 1);
     const int m = base + tid * R;
     const int mine = m < N ? (m + R <= N ? R : N - m) : 0;
     float r[R];
@@ -1083,14 +994,25 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
       for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
     }
     const float mf = (float)m;
-    for (int k = 0; k < K; ++k) {
-      float cf[NCF], h[R];
-      load_cf(sm.cf + k * NCF, cf);
-      if (win && outside_support(cf, wf, wl)) continue;
-      done += mine;
-      mixed_vals<MODEL, R>(cf, mf, h);
-#pragma unroll
-      for (int j = 0; j < R; ++j) r[j] -= h[j];
+    // components active on this warp's range, ascending (all K without the window)
+    uint32_t act[2];
+    if (win) {
+      const int q = wfirst / (32 * R);
+      act[0] = sm.wmask[2 * q];
+      act[1] = sm.wmask[2 * q + 1];
+    } else {
+      act[0] = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
+      act[1] = K >= 64 ? 0xffffffffu : (K > 32 ? ((1u << (K - 32)) - 1u) : 0u);
+    }
+    done += mine * (__popc(act[0]) + __popc(act[1]));
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      for (uint32_t bits = act[half]; bits; bits &= bits - 1u) {
+        const int k = (half << 5) + __ffs(bits) - 1;
+        float cf[NCF];
+        load_cf(sm.cf + k * NCF, cf);
+        mixed_sub<MODEL, R>(cf, mf, r);
+      }
     }
     // residual energy and the adjoint weights rc = c_n r_n / sigma^2
     float so = 0.f, sn = 0.f;
@@ -1106,10 +1028,12 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     kahan_add(eo_s, eo_c, so);
     kahan_add(en_s, en_c, sn);
     if (GRAD) {
-      for (int k = 0; k < K; ++k) {
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half)
+      for (uint32_t bits = act[half]; bits; bits &= bits - 1u) {
+        const int k = (half << 5) + __ffs(bits) - 1;
         float cf[NCF], o[4];
         load_cf(sm.cf + k * NCF, cf);
-        if (win && outside_support(cf, wf, wl)) continue;
         mixed_adj<MODEL, R>(cf, mf, r, o);
 #pragma unroll
         for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
@@ -1131,10 +1055,12 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
         const int n = m + j;
         cw[j] = n < N ? (n < n1 ? inv_s2_f : beta_f * inv_s2_f) : 0.0f;
       }
-      for (int k = 0; k < K; ++k) {
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half)
+      for (uint32_t bits = act[half]; bits; bits &= bits - 1u) {
+        const int k = (half << 5) + __ffs(bits) - 1;
         float cf[NCF], o[4];
         load_cf(sm.cf + k * NCF, cf);
-        if (win && outside_support(cf, wf, wl)) continue;
         mixed_fis<MODEL, R>(cf, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
 #pragma unroll
         for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
@@ -1264,7 +1190,7 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
 template <int MODEL, int PREC>
 __device__ __forceinline__ double eval_setup(const ProbDev& pb, const PriorArgs& pa, int K,
                                              const double* z, EvalSmem& sm) {
-  if constexpr (PREC == MIXED) return (double)eval_setup_mixed<MODEL>(pb, pa, K, z, sm);
+  if constexpr (PREC == MIXED) return (double)eval_setup_mixed<MODEL, 32>(pb, pa, K, z, sm);
   else return eval_setup_any<MODEL, PREC>(pb, pa, K, z, sm);
 }
 
