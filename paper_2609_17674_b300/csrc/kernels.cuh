@@ -100,7 +100,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) 
   const int K = min(max(io.K[gi], 0), kp.kmax);   // caller array: clamp to the slots
   const double beta = io.beta[prob];
   const double* z = io.z + gi * (int64_t)sp.kd;
-  if (PREC == MIXED) fill_exp_table(sm.exptab);
+  if (PREC == MIXED) init_block_tables(sm, sp.nwr);
   __syncthreads();
   block_eval<MODEL, PREC, R, GRAD, FISHER>(pb, kp.pa, K, beta, z, sm, gbuf, fbuf);
   const int tid = threadIdx.x;
@@ -215,7 +215,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   EvalSmem sm = carve_eval(p, sp, kp.tw);
   double* zs = reinterpret_cast<double*>(p);    // [kd + D]
   const double* zg = kp.z + gi * (int64_t)sp.kd;
-  if (PREC == MIXED) fill_exp_table(sm.exptab);
+  if (PREC == MIXED) init_block_tables(sm, sp.nwr);
   for (int i = tid; i < K * D; i += blockDim.x) zs[i] = zg[i];
   if (move == 1 && tid < D) zs[K * D + tid] = s_znew[tid];
   __syncthreads();
@@ -371,14 +371,6 @@ __device__ __forceinline__ CT warp_dot_minv(const CT* a, const CT* b, const CT* 
   return warp_sum(s);
 }
 
-// One out-of-line copy of the block evaluation for the NUTS kernel, which evaluates at
-// two sites (initial point, every leaf): a single copy keeps the kernel's code small.
-template <int MODEL, int PREC, int R>
-__device__ __noinline__ void nuts_eval(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
-                                       const double* z, EvalSmem& sm, double* g) {
-  block_eval<MODEL, PREC, R, true, false>(pb, pa, K, beta, z, sm, g, nullptr);
-}
-
 template <int MODEL, int PREC, int R>
 __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
   using CT = typename std::conditional<PREC == MIXED, float, double>::type;
@@ -429,10 +421,10 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (tid < 4) s_minv[tid] = (CT)kp.minv[4 * prob + tid];
   const CT* minv = s_minv;
   const double* zg = kp.z + gi * (int64_t)kd;
-  if (PREC == MIXED) fill_exp_table(sm.exptab);
+  if (PREC == MIXED) init_block_tables(sm, sp.nwr);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
-  nuts_eval<MODEL, PREC, R>(pb, kp.pa, K, beta, z1, sm, g1);
+  block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
   double cs_done = sm.scal[3];   // component*samples computed (thread 0)
   // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
   // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
@@ -492,7 +484,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         }
       }
       __syncthreads();
-      nuts_eval<MODEL, PREC, R>(pb, kp.pa, K, beta, z1, sm, g1);
+      block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
       cs_done += sm.scal[3];
       if (warp == 0) {
         CT kin = 0;

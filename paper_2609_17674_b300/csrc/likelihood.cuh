@@ -480,6 +480,14 @@ __device__ __forceinline__ void fill_exp_table(float2* tab) {
   }
 }
 
+// per-block tables of the mixed path, at kernel start (before the first __syncthreads):
+// the 2^(j/64) table and cleared active-component masks (every evaluation leaves them
+// cleared again)
+__device__ __forceinline__ void init_block_tables(EvalSmem& sm, int nwr) {
+  fill_exp_table(sm.exptab);
+  for (int i = threadIdx.x; i < 2 * nwr; i += blockDim.x) sm.wmask[i] = 0u;
+}
+
 // e^x as double-float for x in [-80, 80], FP32 arithmetic only (table-driven method of
 // Tang, ACM TOMS 15(2), 1989): x = n ln2/64 + r with n integer and |r| <= ln2/128,
 // e^x = 2^(n div 64) 2^((n mod 64)/64) e^r, e^r from its Taylor series to r^5.
@@ -904,11 +912,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
   const bool win = MODEL != SINUSOID && pa.window;
   const int span = 32 * R;                      // samples per warp range
-  const int nwr = ((int)pb.n + span - 1) / span;
-  if (win) {
-    for (int i = threadIdx.x; i < 2 * nwr; i += blockDim.x) sm.wmask[i] = 0u;
-    __syncthreads();
-  }
+  const int nwr = ((int)pb.n + span - 1) / span;   // masks arrive cleared
   // one thread per component, packed into as few warps as possible: an FP64 warp
   // instruction costs the same whether 1 or 32 lanes are active
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -1182,6 +1186,10 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     sm.scal[1] = lo;
     sm.scal[2] = ln;
     sm.scal[3] = (double)cnt;
+  }
+  if (win) {   // every warp has left the sample loop (barrier above): clear for the next use
+    const int nwr = (N + 32 * R - 1) / (32 * R);
+    for (int i = tid; i < 2 * nwr; i += blockDim.x) sm.wmask[i] = 0u;
   }
   __syncthreads();
 }
