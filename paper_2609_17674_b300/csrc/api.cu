@@ -404,8 +404,13 @@ tsmc_status temper_resample(Ctx* c, int stage) {
   TemperIO tio{c->lln, c->logw, c->beta, c->logz, c->ess, c->probs, c->cfg.alpha};
   const int tt = P >= 1024 ? 1024 : ((P + 31) / 32) * 32;
   pre(c, KC_TEMPER);
-  k_temper<<<np, tt, 0, c->stream>>>(tio, P);
-  TRY(last_launch(c, "k_temper"));
+  if (c->cfg.precision == TSMC_MIXED) {   // FP32 bisection passes; prefix-sum buffer as scratch
+    k_temper_mixed<<<np, tt, 0, c->stream>>>(tio, P, reinterpret_cast<float*>(c->cw));
+    TRY(last_launch(c, "k_temper_mixed"));
+  } else {
+    k_temper<<<np, tt, 0, c->stream>>>(tio, P);
+    TRY(last_launch(c, "k_temper"));
+  }
   pre(c, KC_RESAMPLE);
   k_resample<<<np, tt, 0, c->stream>>>(c->logw, c->cw, c->anc, c->probs, c->cfg.seed, stage, P);
   TRY(last_launch(c, "k_resample"));

@@ -683,6 +683,93 @@ __global__ void __launch_bounds__(1024) k_temper(TemperIO io, int P) {
   }
 }
 
+// Mixed path: the ESS of each bisection pass in FP32 from d_i = ell_i - max (stored once
+// as FP32), x_i = 2^(delta d_i log2 e); the chosen delta then gets one FP64 pass for
+// the ESS, the log-weights and the evidence increment, as above.
+__device__ void ess_sums_f32(const float* d, int P, float delta, float* redf, float& s1,
+                             float& s2) {
+  float a = 0.f, b = 0.f;
+  const float k = delta * 1.44269504088896341f;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const float x = exp2f(k * d[i]);
+    a += x;
+    b = __fmaf_rn(x, x, b);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) { redf[warp] = a; redf[32 + warp] = b; }
+  __syncthreads();
+  a = 0.f; b = 0.f;
+  for (int w = 0; w < nw; ++w) { a += redf[w]; b += redf[32 + w]; }
+  s1 = a;
+  s2 = b;
+}
+
+__global__ void __launch_bounds__(1024) k_temper_mixed(TemperIO io, int P, float* dscratch) {
+  __shared__ double red[128];
+  __shared__ float redf[64];
+  __shared__ double s_m;
+  const int prob = blockIdx.x;
+  const double* ell = io.ell + (int64_t)prob * P;
+  double* logw = io.logw + (int64_t)prob * P;
+  float* d = dscratch + (int64_t)prob * P;
+  const double beta = io.beta[prob];
+  if (beta >= 1.0) {
+    if (threadIdx.x == 0) io.probs[prob].done = 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) logw[i] = 0.0;
+    return;
+  }
+  double mx = -INFINITY;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double e = ell[i];
+    if (isfinite(e) && e > mx) mx = e;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    s_m = m;
+  }
+  __syncthreads();
+  const double m = s_m;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double e = ell[i];
+    d[i] = isfinite(e) ? (float)(e - m) : -INFINITY;
+  }
+  __syncthreads();
+  const double target = io.alpha * (double)P;
+  const double dmax = 1.0 - beta;
+  float a, b;
+  ess_sums_f32(d, P, (float)dmax, redf, a, b);
+  double delta;
+  bool to_one = false;
+  if ((double)a * (double)a / (double)b >= target) {
+    delta = dmax;
+    to_one = true;
+  } else {
+    double lo = 0.0, hi = dmax;
+    for (int it = 0; it < 100; ++it) {
+      if (hi - lo < 1e-14) break;
+      const double mid = 0.5 * (lo + hi);
+      ess_sums_f32(d, P, (float)mid, redf, a, b);
+      if ((double)a * (double)a / (double)b >= target) lo = mid; else hi = mid;
+    }
+    delta = lo > 0.0 ? lo : hi;
+  }
+  double s1, s2;
+  ess_sums(ell, P, m, delta, red, s1, s2);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) logw[i] = delta * ell[i];
+  if (threadIdx.x == 0) {
+    io.beta[prob] = to_one ? 1.0 : beta + delta;
+    io.logz[prob] += (delta * m + log(s1)) - log((double)P);
+    io.ess[prob] = s1 * s1 / s2;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Systematic resampling (one block per problem): FP64 inclusive scan of
 // W_i = exp(logw_i - max), U from Philox, a_i = min{j : C_j > (i+U)/P C_P}.

@@ -428,3 +428,20 @@ def test_state_errors_and_constant_ell():
     assert lz[0] == pytest.approx(-0.5 * np.sum(d * d) / 0.01, rel=1e-12)
     anc = ctx2.get_ancestors().cpu().numpy()
     assert np.array_equal(anc, np.arange(512))
+
+
+def test_mixed_temper_matches_oracle():
+    """The mixed path's FP32 bisection passes choose the same beta as the FP64 definition
+    (to the precision of an FP32 ESS) and the FP64 evidence increment."""
+    wl = synth.config2(P=8192)
+    z, K = synth.prior_population(wl, 3)
+    t = torch()
+    ctx = sampler.open_context(wl, capi.MIXED)
+    ctx.set_population(dev_tensor(z, t.float64), dev_tensor(K, t.int32), beta=[0.0])
+    _, _, _, ln = ctx.get_population()
+    ell = ln.cpu().numpy()
+    b, lz, e = ctx.temper_reweight_resample(2)
+    bo, inco, esso, _ = oracle.temper(ell, wl.alpha, 0.0)
+    assert b[0] == pytest.approx(bo, rel=1e-5)
+    assert e[0] == pytest.approx(esso, rel=1e-3)
+    assert lz[0] == pytest.approx(inco, rel=1e-4, abs=1e-4)
