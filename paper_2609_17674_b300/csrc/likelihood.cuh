@@ -197,105 +197,152 @@ __device__ __forceinline__ void mixed_vals(const float* cf, float m, float (&h)[
   }
 }
 
-// r_j -= h(t_{m+j}) for one component on the thread's R samples (fused multiply-adds)
+// ---------------------------------------------------------------------------
+// Packed sample registers of the mixed likelihood loop.  A thread's R residuals
+// are R/2 float2 pairs so that one packed FP32 instruction (FFMA2 / FMUL2 /
+// FADD2 of the sm_100 family) advances two independent recurrences per issue
+// slot.  Pair i, half h holds local sample pair_sample(i, h):
+//   pulse:    (j, j + 8) inside each run of 16 samples: the two halves are two
+//             8-sample chunks with their own anchors, stepped in lockstep; every
+//             element sees exactly the operations of the scalar recurrence
+//   sinusoid: (i, i + R/2): two rotation chains, each with its own phase anchor
+// ---------------------------------------------------------------------------
 template <int MODEL, int R>
-__device__ __forceinline__ void mixed_sub(const float* cf, float m, float (&r)[R]) {
+__host__ __device__ constexpr int pair_sample(int i, int h) {
+  return MODEL == SINUSOID ? i + h * (R / 2) : ((i >> 3) << 4) + (h << 3) + (i & 7);
+}
+template <int MODEL, int R>
+__host__ __device__ constexpr int sample_pair(int s) {
+  return MODEL == SINUSOID ? s % (R / 2) : ((s >> 4) << 3) + (s & 7);
+}
+template <int MODEL, int R>
+__host__ __device__ constexpr int sample_half(int s) {
+  return MODEL == SINUSOID ? s / (R / 2) : (s >> 3) & 1;
+}
+template <int MODEL, int R>
+__device__ __forceinline__ float& slot(float2 (&r)[R / 2], int s) {
+  return sample_half<MODEL, R>(s) ? r[sample_pair<MODEL, R>(s)].y
+                                  : r[sample_pair<MODEL, R>(s)].x;
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// r -= h(t_{m+s}) for one component on the thread's R samples (packed pairs)
+template <int MODEL, int R>
+__device__ __forceinline__ void mixed_sub(const float* cf, float m, float2 (&r)[R / 2]) {
+  static_assert(R % 16 == 0, "packed pulse chunks need R a multiple of 16");
   if (MODEL == SINUSOID) {
-    float c, s;
-    sin_anchor(cf, m, c, s);
-    const float nA = -cf[0], rc = cf[5], rs = cf[6];
+    float2 c, s;
+    sin_anchor(cf, m, c.x, s.x);
+    sin_anchor(cf, m + (float)(R / 2), c.y, s.y);
+    const float2 nA = f2(-cf[0]), rc = f2(cf[5]), rs = f2(cf[6]), nrs = f2(-cf[6]);
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      r[j] = __fmaf_rn(nA, c, r[j]);
-      const float c2 = __fmaf_rn(c, rc, -s * rs);
-      s = __fmaf_rn(s, rc, c * rs);
+    for (int j = 0; j < R / 2; ++j) {
+      r[j] = __ffma2_rn(nA, c, r[j]);
+      const float2 c2 = __ffma2_rn(c, rc, __fmul2_rn(s, nrs));
+      s = __ffma2_rn(s, rc, __fmul2_rn(c, rs));
       c = c2;
     }
   } else {
-    const float nA = -cf[0];
-    const float v00 = dd_axpy(cf[1], cf[2], cf[3], cf[4], m);
+    const float2 nA = f2(-cf[0]), del = f2(cf[3]), rho = f2(cf[5]);
+    const float2 v00 = f2(dd_axpy(cf[1], cf[2], cf[3], cf[4], m));
     if (cf[8] != 0.0f) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const float v = __fmaf_rn((float)j, cf[3], v00);
-        r[j] = __fmaf_rn(nA, ex2a(-v * v), r[j]);
+      for (int i = 0; i < R / 2; ++i) {
+        const float2 v = __ffma2_rn(make_float2((float)pair_sample<MODEL, R>(i, 0),
+                                                (float)pair_sample<MODEL, R>(i, 1)), del, v00);
+        r[i] = __ffma2_rn(nA, make_float2(ex2a(-v.x * v.x), ex2a(-v.y * v.y)), r[i]);
       }
     } else {
 #pragma unroll
-      for (int c8 = 0; c8 < R / 8; ++c8) {
-        const float v0 = __fmaf_rn((float)(8 * c8), cf[3], v00);
-        float g = ex2a(-v0 * v0);
-        float q = ex2a(fminf(-__fmaf_rn(v0, cf[6], cf[7]), 64.0f));
+      for (int p = 0; p < R / 16; ++p) {
+        const float2 v0 = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del, v00);
+        float2 g = make_float2(ex2a(-v0.x * v0.x), ex2a(-v0.y * v0.y));
+        float2 q = make_float2(ex2a(fminf(-__fmaf_rn(v0.x, cf[6], cf[7]), 64.0f)),
+                               ex2a(fminf(-__fmaf_rn(v0.y, cf[6], cf[7]), 64.0f)));
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          r[8 * c8 + j] = __fmaf_rn(nA, g, r[8 * c8 + j]);
-          g *= q;
-          q *= cf[5];
+          r[8 * p + j] = __ffma2_rn(nA, g, r[8 * p + j]);
+          g = __fmul2_rn(g, q);
+          q = __fmul2_rn(q, rho);
         }
       }
     }
   }
 }
 
-// adjoint partial sums of one component over the thread's samples (rc = c_n r_n / sigma^2)
+// adjoint partial sums of one component over the thread's samples (rc = c_n r_n / sigma^2,
+// packed pairs as above)
 //   pulse:    s0 = sum rc g, s1 = sum rc g v, s2 = sum rc g v^2
 //   sinusoid: s0 = sum rc cos, s1 = sum rc sin, s2 = sum rc sin n, s3 = sum rc sin n^2
 template <int MODEL, int R>
-__device__ __forceinline__ void mixed_adj(const float* cf, float m, const float (&rc)[R],
+__device__ __forceinline__ void mixed_adj(const float* cf, float m, const float2 (&rc)[R / 2],
                                           float (&o)[4]) {
   if (MODEL == SINUSOID) {
-    float c, s;
-    sin_anchor(cf, m, c, s);
-    const float rcs = cf[5], rsn = cf[6];
-    float sc = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    float2 c, s;
+    const float mh = m + (float)(R / 2);
+    sin_anchor(cf, m, c.x, s.x);
+    sin_anchor(cf, mh, c.y, s.y);
+    const float2 rcs = f2(cf[5]), rsn = f2(cf[6]), nrsn = f2(-cf[6]);
+    float2 sc = f2(0.f), u0 = f2(0.f), u1 = f2(0.f), u2 = f2(0.f);
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      sc = __fmaf_rn(rc[j], c, sc);
-      const float p = rc[j] * s;
-      u0 += p;
-      u1 = __fmaf_rn(p, (float)j, u1);
-      u2 = __fmaf_rn(p, (float)(j * j), u2);
-      const float c2 = __fmaf_rn(c, rcs, -s * rsn);
-      s = __fmaf_rn(s, rcs, c * rsn);
+    for (int j = 0; j < R / 2; ++j) {
+      sc = __ffma2_rn(rc[j], c, sc);
+      const float2 p = __fmul2_rn(rc[j], s);
+      u0 = __fadd2_rn(u0, p);
+      u1 = __ffma2_rn(p, f2((float)j), u1);
+      u2 = __ffma2_rn(p, f2((float)(j * j)), u2);
+      const float2 c2 = __ffma2_rn(c, rcs, __fmul2_rn(s, nrsn));
+      s = __ffma2_rn(s, rcs, __fmul2_rn(c, rsn));
       c = c2;
     }
-    o[0] = sc;
-    o[1] = u0;
-    o[2] = __fmaf_rn(m, u0, u1);
-    o[3] = __fmaf_rn(m, __fmaf_rn(m, u0, 2.0f * u1), u2);
+    o[0] = sc.x + sc.y;
+    o[1] = u0.x + u0.y;
+    o[2] = __fmaf_rn(m, u0.x, u1.x) + __fmaf_rn(mh, u0.y, u1.y);
+    o[3] = __fmaf_rn(m, __fmaf_rn(m, u0.x, 2.0f * u1.x), u2.x) +
+           __fmaf_rn(mh, __fmaf_rn(mh, u0.y, 2.0f * u1.y), u2.y);
   } else {
-    const float v00 = dd_axpy(cf[1], cf[2], cf[3], cf[4], m);
+    const float2 del = f2(cf[3]), rho = f2(cf[5]);
+    const float2 v00 = f2(dd_axpy(cf[1], cf[2], cf[3], cf[4], m));
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     if (cf[8] != 0.0f) {
+      float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f);
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const float v = __fmaf_rn((float)j, cf[3], v00);
-        const float p = rc[j] * ex2a(-v * v);
-        s0 += p;
-        s1 = __fmaf_rn(p, v, s1);
-        s2 = __fmaf_rn(p * v, v, s2);
+      for (int i = 0; i < R / 2; ++i) {
+        const float2 v = __ffma2_rn(make_float2((float)pair_sample<MODEL, R>(i, 0),
+                                                (float)pair_sample<MODEL, R>(i, 1)), del, v00);
+        const float2 p = __fmul2_rn(rc[i], make_float2(ex2a(-v.x * v.x), ex2a(-v.y * v.y)));
+        a0 = __fadd2_rn(a0, p);
+        a1 = __ffma2_rn(p, v, a1);
+        a2 = __ffma2_rn(__fmul2_rn(p, v), v, a2);
       }
+      s0 = a0.x + a0.y;
+      s1 = a1.x + a1.y;
+      s2 = a2.x + a2.y;
     } else {
-      const float del = cf[3], del2 = cf[7], rho = cf[5];
+      const float2 del2 = f2(cf[7]), twodel = f2(2.0f * cf[3]);
 #pragma unroll
-      for (int c8 = 0; c8 < R / 8; ++c8) {
-        const float v0 = __fmaf_rn((float)(8 * c8), del, v00);
-        float g = ex2a(-v0 * v0);
-        float q = ex2a(fminf(-__fmaf_rn(v0, cf[6], del2), 64.0f));
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int p = 0; p < R / 16; ++p) {
+        const float2 v0 = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del, v00);
+        float2 g = make_float2(ex2a(-v0.x * v0.x), ex2a(-v0.y * v0.y));
+        float2 q = make_float2(ex2a(fminf(-__fmaf_rn(v0.x, cf[6], cf[7]), 64.0f)),
+                               ex2a(fminf(-__fmaf_rn(v0.y, cf[6], cf[7]), 64.0f)));
+        float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float p = rc[8 * c8 + j] * g;
-          a0 += p;
-          a1 = __fmaf_rn(p, (float)j, a1);
-          a2 = __fmaf_rn(p, (float)(j * j), a2);
-          g *= q;
-          q *= rho;
+          const float2 pr = __fmul2_rn(rc[8 * p + j], g);
+          a0 = __fadd2_rn(a0, pr);
+          a1 = __ffma2_rn(pr, f2((float)j), a1);
+          a2 = __ffma2_rn(pr, f2((float)(j * j)), a2);
+          g = __fmul2_rn(g, q);
+          q = __fmul2_rn(q, rho);
         }
-        // sum p v = v0 a0 + del a1;  sum p v^2 = v0^2 a0 + 2 v0 del a1 + del^2 a2
-        s0 += a0;
-        s1 += __fmaf_rn(v0, a0, del * a1);
-        s2 += __fmaf_rn(v0, __fmaf_rn(v0, a0, 2.0f * del * a1), del2 * a2);
+        // per chunk: sum p v = v0 a0 + del a1;  sum p v^2 = v0^2 a0 + 2 v0 del a1 + del^2 a2
+        const float2 c1 = __ffma2_rn(v0, a0, __fmul2_rn(del, a1));
+        const float2 c2 = __ffma2_rn(v0, __ffma2_rn(v0, a0, __fmul2_rn(twodel, a1)),
+                                     __fmul2_rn(del2, a2));
+        s0 += a0.x; s0 += a0.y;            // chunks in sample order
+        s1 += c1.x; s1 += c1.y;
+        s2 += c2.x; s2 += c2.y;
       }
     }
     o[0] = s0; o[1] = s1; o[2] = s2; o[3] = 0.f;
@@ -985,17 +1032,20 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     if (wfirst >= N) continue;  // whole warp past the end (warp-uniform)
     const int m = base + tid * R;
     const int mine = m < N ? (m + R <= N ? R : N - m) : 0;
-    float r[R];
+    float2 r[R / 2];    // packed pairs (pair_sample layout)
     if (m + R <= N) {
       const float4* src = reinterpret_cast<const float4*>(pb.d32 + m);
 #pragma unroll
       for (int q = 0; q < R / 4; ++q) {
         const float4 v = src[q];
-        r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+        slot<MODEL, R>(r, 4 * q) = v.x;
+        slot<MODEL, R>(r, 4 * q + 1) = v.y;
+        slot<MODEL, R>(r, 4 * q + 2) = v.z;
+        slot<MODEL, R>(r, 4 * q + 3) = v.w;
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
+      for (int j = 0; j < R; ++j) slot<MODEL, R>(r, j) = (m + j < N) ? pb.d32[m + j] : 0.0f;
     }
     const float mf = (float)m;
     // components active on this warp's range, ascending (all K without the window)
@@ -1021,13 +1071,14 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     // residual energy and the adjoint weights rc = c_n r_n / sigma^2
     float so = 0.f, sn = 0.f;
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
+    for (int j = 0; j < R; ++j) {       // sample order
       const int n = m + j;
       const bool valid = n < N, old = n < n1;
-      const float rr = valid ? r[j] : 0.0f;
+      float& rj = slot<MODEL, R>(r, j);
+      const float rr = valid ? rj : 0.0f;
       const float e = rr * rr;
       if (old) so += e; else sn += e;
-      r[j] = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
+      rj = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
     }
     kahan_add(eo_s, eo_c, so);
     kahan_add(en_s, en_c, sn);
