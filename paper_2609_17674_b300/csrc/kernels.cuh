@@ -86,13 +86,26 @@ struct EvalIO {
 // (32 samples per thread) or 3 (16 samples per thread) resident blocks per SM
 #define TSMC_PARTICLE_BOUNDS __launch_bounds__(256, (PREC == MIXED && R == 16) ? 3 : 2)
 
+// The problem descriptor is copied to shared memory once per block: its fields are
+// read where they are used instead of holding ~70 registers across the kernel.
+__device__ __forceinline__ const ProbDev& stage_problem(const ProbDev* probs, int prob,
+                                                        ProbDev& s) {
+  static_assert(sizeof(ProbDev) % 8 == 0, "ProbDev is copied as 8-byte words");
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(probs + prob);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(&s);
+  for (int i = threadIdx.x; i < (int)(sizeof(ProbDev) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return s;
+}
+
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
 __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
-  const ProbDev pb = kp.probs[prob];
+  __shared__ ProbDev s_pb;
+  const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
   char* p = smem;
   EvalSmem sm = carve_eval(p, sp, kp.tw);
   double* gbuf = reinterpret_cast<double*>(p);   // [kd] gradient staging
@@ -169,7 +182,8 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const uint64_t li = (uint64_t)(gi % kp.P);
-  const ProbDev pb = kp.probs[prob];
+  __shared__ ProbDev s_pb;
+  const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
   if (pb.done) return;
   const int stage = *kp.stage;
   const int K = min(max(kp.K[gi], 0), kp.kmax);
@@ -382,7 +396,8 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const uint64_t li = (uint64_t)(gi % kp.P);
-  const ProbDev pb = kp.probs[prob];
+  __shared__ ProbDev s_pb;
+  const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
   if (pb.done) return;
   const int stage = *kp.stage;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

@@ -794,6 +794,48 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
+// Warp totals of o[0..3], one value per group of 8 lanes: on return lane l holds the
+// total of o[l >> 3].  Each total uses the pairing of the butterfly tree (offsets 16,
+// 8, 4, 2, 1), so it equals warp_sum(o[v]) bit for bit, in 6 shuffles instead of 20.
+__device__ __forceinline__ float warp_sum4_split(const float (&o)[4], int lane) {
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+  float k0 = b4 ? o[2] : o[0];
+  float k1 = b4 ? o[3] : o[1];
+  const float s0 = b4 ? o[0] : o[2];
+  const float s1 = b4 ? o[1] : o[3];
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  float k = b3 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, b3 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// adds the warp totals of o[0..D-1] for component k to the warp's shared Kahan row
+// acc[k*D + d] = (sum, compensation)
+template <int D>
+__device__ __forceinline__ void warp_accumulate(const float (&o)[4], int lane, int k,
+                                                float2* acc) {
+  if (D == 1) {
+    const float v = warp_sum(o[0]);
+    if (lane == 0) {
+      float2 a = acc[k];
+      kahan_add(a.x, a.y, v);
+      acc[k] = a;
+    }
+  } else {
+    const float v = warp_sum4_split(o, lane);
+    const int d = lane >> 3;
+    if ((lane & 7) == 0 && d < D) {
+      float2 a = acc[k * D + d];
+      kahan_add(a.x, a.y, v);
+      acc[k * D + d] = a;
+    }
+  }
+}
+
 __device__ __forceinline__ void load_cf(const float* cf, float (&o)[NCF]) {
   const float4* c4 = reinterpret_cast<const float4*>(cf);
 #pragma unroll
@@ -1018,11 +1060,16 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
   const int N = (int)pb.n, n1 = (int)pb.n1;
   const float beta_f = (float)beta, inv_s2_f = (float)pb.inv_s2;
   float eo_s = 0.f, eo_c = 0.f, en_s = 0.f, en_c = 0.f;   // Kahan energies
-  float gs[2][4], gc[2][4], fs[2][4], fc[2][4];           // Kahan slot sums
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int d = 0; d < 4; ++d) gs[q][d] = gc[q][d] = fs[q][d] = fc[q][d] = 0.f;
+  // per-warp Kahan rows (sum, compensation) of the component partial sums; only
+  // this warp touches its rows until the barrier after the sample loop
+  const int KDm = K * D;
+  float2* const gacc = sm.wacc2() + warp * KDm;
+  float2* const facc = FISHER ? sm.wfis2() + warp * KDm : nullptr;
+  for (int i = lane; i < KDm; i += 32) {
+    if (GRAD) gacc[i] = make_float2(0.f, 0.f);
+    if (FISHER) facc[i] = make_float2(0.f, 0.f);
+  }
+  __syncwarp();
   const bool win = MODEL != SINUSOID && pa.window;
   int done = 0;   // component*samples this thread computed
 
@@ -1090,17 +1137,7 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
         float cf[NCF], o[4];
         load_cf(sm.cf + k * NCF, cf);
         mixed_adj<MODEL, R>(cf, mf, r, o);
-#pragma unroll
-        for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
-        if (lane == (k & 31)) {
-          if (k < 32) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) kahan_add(gs[0][d], gc[0][d], o[d]);
-          } else {
-#pragma unroll
-            for (int d = 0; d < D; ++d) kahan_add(gs[1][d], gc[1][d], o[d]);
-          }
-        }
+        warp_accumulate<D>(o, lane, k, gacc);
       }
     }
     if (FISHER) {
@@ -1117,32 +1154,13 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
         float cf[NCF], o[4];
         load_cf(sm.cf + k * NCF, cf);
         mixed_fis<MODEL, R>(cf, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
-#pragma unroll
-        for (int d = 0; d < D; ++d) o[d] = warp_sum(o[d]);
-        if (lane == (k & 31)) {
-          if (k < 32) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) kahan_add(fs[0][d], fc[0][d], o[d]);
-          } else {
-#pragma unroll
-            for (int d = 0; d < D; ++d) kahan_add(fs[1][d], fc[1][d], o[d]);
-          }
-        }
+        warp_accumulate<D>(o, lane, k, facc);
       }
     }
   }
 
-  // ---- per-warp slot sums (double-float: hi = s, lo = -c) -> shared -> components ----
+  // ---- per-warp Kahan rows (double-float: hi = s, lo = -c) -> components ----
   if (GRAD || FISHER) {
-    const int KDm = K * D;
-    for (int k = lane; k < K; k += 32) {
-      const int q = k < 32 ? 0 : 1;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (GRAD) sm.wacc2()[warp * KDm + k * D + d] = make_float2(gs[q][d], -gc[q][d]);
-        if (FISHER) sm.wfis2()[warp * KDm + k * D + d] = make_float2(fs[q][d], -fc[q][d]);
-      }
-    }
     __syncthreads();
     const float* th = sm.fth();
     for (int k = tid; k < K; k += blockDim.x) {
@@ -1152,8 +1170,8 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
       for (int w = 0; w < nw; ++w) {
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          if (GRAD) { const float2 v = sm.wacc2()[w * KDm + k * D + d]; S[d] = df_add(S[d], DF{v.x, v.y}); }
-          if (FISHER) { const float2 v = sm.wfis2()[w * KDm + k * D + d]; F[d] = df_add(F[d], DF{v.x, v.y}); }
+          if (GRAD) { const float2 v = sm.wacc2()[w * KDm + k * D + d]; S[d] = df_add(S[d], DF{v.x, -v.y}); }
+          if (FISHER) { const float2 v = sm.wfis2()[w * KDm + k * D + d]; F[d] = df_add(F[d], DF{v.x, -v.y}); }
         }
       }
       const float A = th[k * D];
