@@ -393,6 +393,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   __shared__ int s_flag[8];
   __shared__ double s_ctl[8];
   __shared__ CT s_minv[4];
+  __shared__ double s_uleaf;   // uniform of the next leaf's multinomial choice
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const uint64_t li = (uint64_t)(gi % kp.P);
@@ -419,10 +420,10 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   char* p = smem;
   EvalSmem sm = carve_eval(p, sp, kp.tw);
   const int kd = sp.kd;
-  // positions (FP64) and the evaluation's gradient output (FP64)
+  // positions (FP64) and the evaluation's gradient output (CT, in an 8-byte slot)
   double* vd = reinterpret_cast<double*>(p);
   double *zc = vd, *z1 = vd + kd, *zL = vd + 2 * kd, *zR = vd + 3 * kd, *sz = vd + 4 * kd;
-  double* g1 = vd + 5 * kd;
+  CT* g1 = reinterpret_cast<CT*>(vd + 5 * kd);
   // momenta, gradients at the ends, momentum sums and checkpoints (CT), one slot of
   // 8 bytes per element each so the layout does not depend on CT
   CT* vc = reinterpret_cast<CT*>(vd + 6 * kd);
@@ -439,7 +440,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (PREC == MIXED) init_block_tables(sm, sp.nwr);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
-  block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+  block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
   double cs_done = sm.scal[3];   // component*samples computed (thread 0)
   // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
   // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
@@ -451,7 +452,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
                     momentum_normal<CT>(kp.seed, prob, li, stage, round, (uint64_t)i);
       pL[i] = pm; pR[i] = pm; rho[i] = pm;
       zL[i] = zc[i]; zR[i] = zc[i];
-      gL[i] = (CT)g1[i]; gR[i] = (CT)g1[i];
+      gL[i] = g1[i]; gR[i] = g1[i];
     }
     __syncwarp();
     CT kin = 0;
@@ -482,7 +483,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       const double* zs0 = dir > 0 ? zR : zL;
       const CT *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
       for (int i = lane; i < n; i += 32) {
-        z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = (double)gs0[i]; srho[i] = 0;
+        z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0;
       }
     }
     __syncthreads();
@@ -492,19 +493,24 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
     for (int l = 0; l < nsub; ++l) {
       if (warp == 0) {
         for (int i = lane; i < n; i += 32) {
-          const CT ph = p1[i] + (CT)0.5 * de_c * (CT)g1[i];
+          const CT ph = p1[i] + (CT)0.5 * de_c * g1[i];
           p1[i] = ph;
           if (PREC == FP64) z1[i] = z1[i] + de * (double)minv[i % D] * (double)ph;
           else z1[i] = z1[i] + (double)(de_c * minv[i % D] * ph);
         }
       }
+      if (l > 0 && tid == blockDim.x - 1) {   // the leaf's uniform, off the control path
+        const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_LEAF,
+                             (uint64_t)((nsub - 1) + l));
+        s_uleaf = u01(w.w[0]);
+      }
       __syncthreads();
-      block_eval<MODEL, PREC, R, true, false>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
-      cs_done += sm.scal[3];
+      block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+      if (tid == 0) cs_done += sm.scal[3];
       if (warp == 0) {
         CT kin = 0;
         for (int i = lane; i < n; i += 32) {
-          const CT pn = p1[i] + (CT)0.5 * de_c * (CT)g1[i];
+          const CT pn = p1[i] + (CT)0.5 * de_c * g1[i];
           p1[i] = pn;
           kin += minv[i % D] * pn * pn;
         }
@@ -525,11 +531,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
             const double lw = -H;
             const double nl = lae<CT>(s_ctl[5], lw);
             take = (l == 0);
-            if (!take) {
-              const int leaf_id = (nsub - 1) + l;
-              const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_LEAF, (uint64_t)leaf_id);
-              take = u01(w.w[0]) < (double)ct_exp((CT)(lw - nl));
-            }
+            if (!take) take = s_uleaf < (double)ct_exp((CT)(lw - nl));
             if (take) { s_ctl[6] = sm.scal[1]; s_ctl[7] = sm.scal[2]; }
             s_ctl[5] = nl;
           }
@@ -575,7 +577,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       const int dir = s_flag[2];
       double* ze = dir > 0 ? zR : zL;
       CT *pe = dir > 0 ? pR : pL, *ge = dir > 0 ? gR : gL;
-      for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = (CT)g1[i]; }
+      for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = g1[i]; }
       int take = 0;
       if (lane == 0) {
         const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_TOP, (uint64_t)depth);

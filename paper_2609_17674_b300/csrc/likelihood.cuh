@@ -570,8 +570,12 @@ __device__ __forceinline__ DF df_exp(DF x, const float2* tab) {
 
 // theta of parameter d from an FP64 coordinate, as double-float (uniform or log-uniform
 // map), with s(z) and 1 - s(z) both from e^{-|z|}; also returns dtheta/dz in FP32
+struct Coord32 { float th, dth, lp, pg, pc; };
+
+// theta in double-float; with pr != nullptr also the log prior density of z and its
+// first two derivatives (lp, pg, pc of Coord32) from the same e^{-|z|} and 1/(1+e)
 __device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, double z, const float2* tab,
-                                       float& dth) {
+                                       float& dth, Coord32* pr = nullptr) {
   const float zh = (float)z;
   const DF az = zh >= 0.f ? DF{zh, (float)(z - (double)zh)} : DF{-zh, -(float)(z - (double)zh)};
   const DF e = df_exp(df_neg(az), tab);              // e^{-|z|}
@@ -579,6 +583,12 @@ __device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, double z, const
   const DF eq = df_mul(e, q);
   const DF s = z >= 0.0 ? q : eq;                    // s(z)
   const float ds = __fmul_rn(q.hi, eq.hi);           // s (1 - s)
+  if (pr) {
+    const float sc = z >= 0.0 ? eq.hi : q.hi;        // 1 - s
+    pr->lp = -az.hi - 2.f * log1pf(e.hi);
+    pr->pg = sc - s.hi;
+    pr->pc = 2.f * ds;
+  }
   const DF span = df_from(pb.f_span[d]);
   DF th = df_add(df_from(pb.f_off[d]), df_mul(span, s));
   if (pb.logmask & (1u << d)) {
@@ -642,8 +652,6 @@ __device__ __forceinline__ void finish_fisher(int prec, const double* th, const 
 // below the path's tolerance: amplitudes, widths, frequency derivative, phase)
 // ---------------------------------------------------------------------------
 
-struct Coord32 { float th, dth, lp, pg, pc; };
-
 __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& pa, int d, float z) {
   Coord32 c;
   if (pa.model == PULSE_LINAMP) {
@@ -662,13 +670,12 @@ __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& p
   const float s = z >= 0.f ? q : e * q;
   const float sc = z >= 0.f ? e * q : q;
   const float ds = s * sc;
+  const float off = pb.f_off[d].x, span = pb.f_span[d].x;   // FP32 roundings of the bounds
   if (pb.logmask & (1u << d)) {
-    const float llo = (float)pb.llo[d], span = (float)(pb.lhi[d] - pb.llo[d]);
-    c.th = expf(llo + span * s);
+    c.th = expf(off + span * s);
     c.dth = c.th * span * ds;
   } else {
-    const float lo = (float)pb.lo[d], span = (float)(pb.hi[d] - pb.lo[d]);
-    c.th = lo + span * s;
+    c.th = off + span * s;
     c.dth = span * ds;
   }
   c.lp = -a - 2.f * log1pf(e);
@@ -990,8 +997,9 @@ __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, d
 
 // ---------------------------------------------------------------------------
 // Mixed path: setup, evaluation and reductions in FP32 (double-float where a
-// total needs more than 24 bits); FP64 only for the centre/width/frequency maps,
-// the template anchors and the final scalars of thread 0.
+// total needs more than 24 bits; pulse centre and width in double-float); FP64
+// only for the sinusoid frequency map and phase constants and the final scalars.
+// The serial parts run one thread per (component, parameter) where they can.
 // ---------------------------------------------------------------------------
 template <int MODEL, int R>
 __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const double* z,
@@ -999,43 +1007,53 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   constexpr int D = model_d<MODEL>();
   float lp = 0.f;
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
+  const int KD = K * D;
+  float* th_lo = th + KD;       // double-float low parts of the pulse centre and width
   const bool win = MODEL != SINUSOID && pa.window;
   const int span = 32 * R;                      // samples per warp range
   const int nwr = ((int)pb.n + span - 1) / span;   // masks arrive cleared
-  // one thread per component, packed into as few warps as possible: an FP64 warp
-  // instruction costs the same whether 1 or 32 lanes are active
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const double* zk = z + k * D;
-    float t[4];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const Coord32 c = coord32(pb, pa, d, (float)zk[d]);
-      t[d] = c.th;
-      th[k * D + d] = c.th;
-      dth[k * D + d] = c.dth;
-      pgv[k * D + d] = c.pg;
-      pcv[k * D + d] = c.pc;
+  // (1) one thread per (component, parameter): coordinate map, Jacobian, prior terms
+  for (int i = threadIdx.x; i < KD; i += blockDim.x) {
+    const int d = i % D;
+    const double zi = z[i];
+    if (MODEL == PULSE && d > 0) {
+      // centre and width to ~1e-12 relative in double-float (FP32 pipe, no FP64)
+      Coord32 c;
+      const DF t = theta_df(pb, d, zi, sm.exptab, c.dth, &c);
+      th[i] = t.hi;
+      th_lo[i] = t.lo;
+      dth[i] = c.dth;
+      pgv[i] = c.pg;
+      pcv[i] = c.pc;
       lp += c.lp;
+    } else {
+      const Coord32 c = coord32(pb, pa, d, (float)zi);
+      th[i] = c.th;
+      dth[i] = c.dth;
+      pgv[i] = c.pg;
+      pcv[i] = c.pc;
+      lp += c.lp;
+      if (MODEL == SINUSOID && d == 1) {   // frequency in FP64 for the phase constants
+        double d1;
+        sm.wacc[i / D] = theta64(pb, 1, zi, d1);   // scratch until the sample loop
+        dth[i] = (float)d1;
+      }
     }
+  }
+  __syncthreads();
+  // (2) one thread per component: path constants and the warp ranges it reaches
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
     float* cf = sm.cf + k * NCF;
     if (MODEL == SINUSOID) {
-      double d1;
-      const double f = theta64(pb, 1, zk[1], d1);
-      dth[k * D + 1] = (float)d1;
-      sin_prep32(t[0], f, t[2], t[3], pb, cf);
+      sin_prep32(th[k * D], sm.wacc[k], th[k * D + 2], th[k * D + 3], pb, cf);
     } else if (MODEL == PULSE) {
-      // centre and width to ~1e-12 relative in double-float (FP32 pipe, no FP64)
-      float d1, d2;
-      const DF t0 = theta_df(pb, 1, zk[1], sm.exptab, d1);
-      const DF w = theta_df(pb, 2, zk[2], sm.exptab, d2);
-      th[k * D + 2] = w.hi;
-      dth[k * D + 1] = d1;
-      dth[k * D + 2] = d2;
-      pulse_prep_df(t[0], t0, w.hi, pb, cf);
+      const float A = th[k * D], w = th[k * D + 2];
+      pulse_prep_df(A, DF{th[k * D + 1], th_lo[k * D + 1]}, w, pb, cf);
+      cf[11] = A / w;                                 // gradient factor A / w
     } else {
-      pulse_prep32(t[0], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
+      pulse_prep32(th[k * D], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
     }
-    if (win) {   // mark the warp ranges that intersect the component's support
+    if (win) {
       const float lo = fmaxf(cf[9], 0.0f), hi = fminf(cf[10], (float)(pb.n - 1));
       if (lo <= hi) {
         const int r0 = (int)lo / span, r1 = min((int)hi / span, nwr - 1);
@@ -1159,73 +1177,8 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     }
   }
 
-  // ---- per-warp Kahan rows (double-float: hi = s, lo = -c) -> components ----
-  if (GRAD || FISHER) {
-    __syncthreads();
-    const float* th = sm.fth();
-    for (int k = tid; k < K; k += blockDim.x) {
-      DF S[4], F[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) { S[d] = DF{0.f, 0.f}; F[d] = DF{0.f, 0.f}; }
-      for (int w = 0; w < nw; ++w) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          if (GRAD) { const float2 v = sm.wacc2()[w * KDm + k * D + d]; S[d] = df_add(S[d], DF{v.x, -v.y}); }
-          if (FISHER) { const float2 v = sm.wfis2()[w * KDm + k * D + d]; F[d] = df_add(F[d], DF{v.x, -v.y}); }
-        }
-      }
-      const float A = th[k * D];
-      if (GRAD) {
-        float g[4];
-        if (MODEL == SINUSOID) {
-          // t_n = t_origin + n dt: sum rc sin t = t_o S1 + dt S2, sum rc sin t^2 = ...
-          const double to = pb.t_origin, dt = pb.dt;
-          const double s1 = df_to_double(S[1]), s2 = df_to_double(S[2]), s3 = df_to_double(S[3]);
-          g[0] = S[0].hi + S[0].lo;
-          g[1] = (float)(-(double)A * kTwoPi * (to * s1 + dt * s2));
-          g[2] = (float)(-(double)A * kPi * (to * to * s1 + 2.0 * to * dt * s2 + dt * dt * s3));
-          g[3] = -A * (S[1].hi + S[1].lo);
-        } else if (MODEL == PULSE) {
-          const float aw = A / th[k * D + 2];
-          g[0] = S[0].hi + S[0].lo;
-          g[1] = aw * (float)kCu * (S[1].hi + S[1].lo);
-          g[2] = aw * (float)(kCu * kCu) * (S[2].hi + S[2].lo);
-        } else {
-          g[0] = S[0].hi + S[0].lo;
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const int i = k * D + d;
-          grad_out[i] = (GT)(g[d] * sm.fdth()[i] + sm.fpg()[i]);
-        }
-      }
-      if (FISHER) {
-        float f[4];
-        if (MODEL == SINUSOID) {
-          const float A2 = A * A;
-          f[0] = F[0].hi + F[0].lo;
-          f[1] = A2 * (float)(kTwoPi * kTwoPi) * (F[1].hi + F[1].lo);
-          f[2] = A2 * (float)(kPi * kPi) * (F[2].hi + F[2].lo);
-          f[3] = A2 * (F[3].hi + F[3].lo);
-        } else if (MODEL == PULSE) {
-          const float aw = A / th[k * D + 2];
-          const float c2 = (float)(kCu * kCu);
-          f[0] = F[0].hi + F[0].lo;
-          f[1] = aw * aw * c2 * (F[1].hi + F[1].lo);
-          f[2] = aw * aw * c2 * c2 * (F[2].hi + F[2].lo);
-        } else {
-          f[0] = F[0].hi + F[0].lo;
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const int i = k * D + d;
-          const float j = sm.fdth()[i];
-          fis_out[i] = (double)(f[d] * j * j + sm.fpc()[i]);
-        }
-      }
-    }
-  }
-  // ---- block totals: energies and log prior as double-float, count as integer ----
+  // ---- block totals, part 1: warp totals of the energies, log prior and count,
+  // taken before the barrier so they overlap the wait for the slowest warp ----
   DF e_o = warp_sum_df(DF{eo_s, -eo_c});
   DF e_n = warp_sum_df(DF{en_s, -en_c});
   DF e_p = warp_sum_df(DF{lp_t, 0.f});
@@ -1240,7 +1193,77 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     ri[warp] = done;
   }
   __syncthreads();
-  if (tid == 0) {
+  // ---- per-warp Kahan rows (double-float: hi = s, lo = -c) -> gradient and metric,
+  // one thread per (component, parameter) ----
+  if (GRAD || FISHER) {
+    const float* th = sm.fth();
+    for (int i = tid; i < KDm; i += blockDim.x) {
+      const int k = i / D, d = i - k * D;
+      const float A = th[k * D];
+      const float aw = MODEL == PULSE ? sm.cf[k * NCF + 11] : 0.f;   // A / w
+      if (GRAD) {
+        float g;
+        if (MODEL == SINUSOID) {
+          // t_n = t_origin + n dt: sum rc sin t = t_o S1 + dt S2, sum rc sin t^2 = ...
+          DF S[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) S[v] = DF{0.f, 0.f};
+          for (int w = 0; w < nw; ++w) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const float2 a = sm.wacc2()[w * KDm + k * D + v];
+              S[v] = df_add(S[v], DF{a.x, -a.y});
+            }
+          }
+          const double to = pb.t_origin, dt = pb.dt;
+          if (d == 0) {
+            g = S[0].hi + S[0].lo;
+          } else if (d == 1) {
+            const double s1 = df_to_double(S[1]), s2 = df_to_double(S[2]);
+            g = (float)(-(double)A * kTwoPi * (to * s1 + dt * s2));
+          } else if (d == 2) {
+            const double s1 = df_to_double(S[1]), s2 = df_to_double(S[2]), s3 = df_to_double(S[3]);
+            g = (float)(-(double)A * kPi * (to * to * s1 + 2.0 * to * dt * s2 + dt * dt * s3));
+          } else {
+            g = -A * (S[1].hi + S[1].lo);
+          }
+        } else {
+          DF S{0.f, 0.f};
+          for (int w = 0; w < nw; ++w) {
+            const float2 a = sm.wacc2()[w * KDm + i];
+            S = df_add(S, DF{a.x, -a.y});
+          }
+          const float c = MODEL == PULSE
+                              ? (d == 0 ? 1.0f : (d == 1 ? aw * (float)kCu
+                                                         : aw * (float)(kCu * kCu)))
+                              : 1.0f;
+          g = c * (S.hi + S.lo);
+        }
+        grad_out[i] = (GT)(g * sm.fdth()[i] + sm.fpg()[i]);
+      }
+      if (FISHER) {
+        DF F{0.f, 0.f};
+        for (int w = 0; w < nw; ++w) {
+          const float2 a = sm.wfis2()[w * KDm + i];
+          F = df_add(F, DF{a.x, -a.y});
+        }
+        float c = 1.0f;
+        if (MODEL == SINUSOID) {
+          const float A2 = A * A;
+          c = d == 0 ? 1.0f : (d == 1 ? A2 * (float)(kTwoPi * kTwoPi)
+                                      : (d == 2 ? A2 * (float)(kPi * kPi) : A2));
+        } else if (MODEL == PULSE) {
+          const float c2 = (float)(kCu * kCu);
+          c = d == 0 ? 1.0f : (d == 1 ? aw * aw * c2 : aw * aw * c2 * c2);
+        }
+        const float f = c * (F.hi + F.lo);
+        const float j = sm.fdth()[i];
+        fis_out[i] = (double)(f * j * j + sm.fpc()[i]);
+      }
+    }
+  }
+  // ---- block totals, part 2: the last thread, beside the component loop ----
+  if (tid == blockDim.x - 1) {
     DF a{0.f, 0.f}, b{0.f, 0.f}, c{0.f, 0.f};
     long long cnt = 0;
     for (int w = 0; w < nw; ++w) {
