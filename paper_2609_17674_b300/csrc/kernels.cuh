@@ -440,57 +440,40 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (PREC == MIXED) init_block_tables(sm, sp.nwr);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
-  block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
-  double cs_done = sm.scal[3];   // component*samples computed (thread 0)
+  double cs_done = 0.0;   // component*samples computed (thread 0)
+  // The evaluation has one call site: iteration l = -1 evaluates the initial point,
+  // then the leaves l = 0 .. 2^depth - 1 of each subtree follow in order.
   // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
   // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
   // s_ctl: 0 H0, 1 logW, 2 sum_acc, 3 cand_lo, 4 cand_ln, 5 sub_logW, 6 sub_lo, 7 sub_ln
   // s_flag: 0 subtree valid, 1 stop, 2 direction, 3 leaves, 4 diverged, 5 depth done
-  if (warp == 0) {
-    for (int i = lane; i < n; i += 32) {
-      const CT pm = sqrt((CT)1 / minv[i % D]) *
-                    momentum_normal<CT>(kp.seed, prob, li, stage, round, (uint64_t)i);
-      pL[i] = pm; pR[i] = pm; rho[i] = pm;
-      zL[i] = zc[i]; zR[i] = zc[i];
-      gL[i] = g1[i]; gR[i] = g1[i];
-    }
-    __syncwarp();
-    CT kin = 0;
-    for (int i = lane; i < n; i += 32) kin += minv[i % D] * pL[i] * pL[i];
-    kin = warp_sum(kin);
-    if (lane == 0) {
-      const double H0 = -sm.scal[0] + 0.5 * (double)kin;
-      s_ctl[0] = H0;
-      s_ctl[1] = -H0;
-      s_ctl[2] = 0.0;
-      s_ctl[3] = sm.scal[1];
-      s_ctl[4] = sm.scal[2];
-      s_flag[3] = 0; s_flag[4] = 0; s_flag[5] = 0;
-    }
-  }
-  for (int depth = 0; depth < kp.max_depth; ++depth) {
+  int depth = 0, l = -1;
+  double de = 0.0;
+  CT de_c = 0;
+  for (;;) {
     const int nsub = 1 << depth;
-    if (warp == 0) {
-      int dir = 0;
-      if (lane == 0) {
-        const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_DIRECTION, (uint64_t)depth);
-        dir = u01(w.w[0]) < 0.5 ? -1 : 1;
-        s_ctl[5] = -INFINITY;
-        s_flag[0] = 1;
-        s_flag[2] = dir;
+    if (l == 0) {   // a new subtree: direction, and the trajectory end it grows from
+      if (warp == 0) {
+        int dir = 0;
+        if (lane == 0) {
+          const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_DIRECTION, (uint64_t)depth);
+          dir = u01(w.w[0]) < 0.5 ? -1 : 1;
+          s_ctl[5] = -INFINITY;
+          s_flag[0] = 1;
+          s_flag[2] = dir;
+        }
+        dir = __shfl_sync(0xffffffffu, dir, 0);
+        const double* zs0 = dir > 0 ? zR : zL;
+        const CT *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
+        for (int i = lane; i < n; i += 32) {
+          z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0;
+        }
       }
-      dir = __shfl_sync(0xffffffffu, dir, 0);
-      const double* zs0 = dir > 0 ? zR : zL;
-      const CT *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
-      for (int i = lane; i < n; i += 32) {
-        z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0;
-      }
+      __syncthreads();
+      de = s_flag[2] * eps;
+      de_c = (CT)de;
     }
-    __syncthreads();
-    const double de = s_flag[2] * eps;
-    const CT de_c = (CT)de;
-    bool valid = true;
-    for (int l = 0; l < nsub; ++l) {
+    if (l >= 0) {   // leapfrog: half step in momentum, full step in position
       if (warp == 0) {
         for (int i = lane; i < n; i += 32) {
           const CT ph = p1[i] + (CT)0.5 * de_c * g1[i];
@@ -505,74 +488,102 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         s_uleaf = u01(w.w[0]);
       }
       __syncthreads();
-      block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
-      if (tid == 0) cs_done += sm.scal[3];
-      if (warp == 0) {
-        CT kin = 0;
-        for (int i = lane; i < n; i += 32) {
-          const CT pn = p1[i] + (CT)0.5 * de_c * g1[i];
-          p1[i] = pn;
-          kin += minv[i % D] * pn * pn;
-        }
-        kin = warp_sum(kin);
-        const double H = -sm.scal[0] + 0.5 * (double)kin;
-        const double H0 = s_ctl[0];
-        int ok = 1, take = 0;
-        if (lane == 0) {
-          s_flag[3] += 1;
-          if (isfinite(H)) {
-            const double a = (double)ct_exp((CT)(H0 - H));
-            s_ctl[2] += a < 1.0 ? a : 1.0;
-          }
-          if (!isfinite(H) || H - H0 > 1000.0) {
-            ok = 0;
-            s_flag[4] = 1;
-          } else {
-            const double lw = -H;
-            const double nl = lae<CT>(s_ctl[5], lw);
-            take = (l == 0);
-            if (!take) take = s_uleaf < (double)ct_exp((CT)(lw - nl));
-            if (take) { s_ctl[6] = sm.scal[1]; s_ctl[7] = sm.scal[2]; }
-            s_ctl[5] = nl;
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        take = __shfl_sync(0xffffffffu, take, 0);
-        if (ok) {
-          if (take)
-            for (int i = lane; i < n; i += 32) sz[i] = z1[i];
-          for (int mm = 1; mm <= depth; ++mm) {
-            if ((l & ((1 << mm) - 1)) == 0) {
-              for (int i = lane; i < n; i += 32) {
-                ckp[mm * kd + i] = p1[i];
-                ckr[mm * kd + i] = srho[i];
-              }
-            }
-          }
-          for (int i = lane; i < n; i += 32) srho[i] += p1[i];
-          __syncwarp();
-          for (int mm = 1; mm <= depth && ok; ++mm) {
-            if (((l + 1) & ((1 << mm) - 1)) == 0) {
-              CT s1 = 0, s2 = 0;
-              for (int i = lane; i < n; i += 32) {
-                const CT seg = srho[i] - ckr[mm * kd + i];
-                const CT mi = minv[i % D];
-                s1 += seg * (mi * ckp[mm * kd + i]);
-                s2 += seg * (mi * p1[i]);
-              }
-              s1 = warp_sum(s1);
-              s2 = warp_sum(s2);
-              if (s1 <= 0 || s2 <= 0) ok = 0;
-            }
-          }
-        }
-        if (lane == 0) s_flag[0] = ok;
-      }
-      __syncthreads();
-      valid = s_flag[0] != 0;
-      if (!valid) break;
     }
-    if (!valid) break;
+    block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+    if (tid == 0) cs_done += sm.scal[3];
+    if (l < 0) {   // initial point: momentum, H0 and both trajectory ends
+      if (warp == 0) {
+        for (int i = lane; i < n; i += 32) {
+          const CT pm = sqrt((CT)1 / minv[i % D]) *
+                        momentum_normal<CT>(kp.seed, prob, li, stage, round, (uint64_t)i);
+          pL[i] = pm; pR[i] = pm; rho[i] = pm;
+          zL[i] = zc[i]; zR[i] = zc[i];
+          gL[i] = g1[i]; gR[i] = g1[i];
+        }
+        __syncwarp();
+        CT kin = 0;
+        for (int i = lane; i < n; i += 32) kin += minv[i % D] * pL[i] * pL[i];
+        kin = warp_sum(kin);
+        if (lane == 0) {
+          const double H0 = -sm.scal[0] + 0.5 * (double)kin;
+          s_ctl[0] = H0;
+          s_ctl[1] = -H0;
+          s_ctl[2] = 0.0;
+          s_ctl[3] = sm.scal[1];
+          s_ctl[4] = sm.scal[2];
+          s_flag[3] = 0; s_flag[4] = 0; s_flag[5] = 0;
+        }
+      }
+      if (kp.max_depth <= 0) break;
+      l = 0;
+      continue;
+    }
+    // ---- leaf: momentum half step, energy, multinomial choice, U-turn checks ----
+    if (warp == 0) {
+      CT kin = 0;
+      for (int i = lane; i < n; i += 32) {
+        const CT pn = p1[i] + (CT)0.5 * de_c * g1[i];
+        p1[i] = pn;
+        kin += minv[i % D] * pn * pn;
+      }
+      kin = warp_sum(kin);
+      const double H = -sm.scal[0] + 0.5 * (double)kin;
+      const double H0 = s_ctl[0];
+      int ok = 1, take = 0;
+      if (lane == 0) {
+        s_flag[3] += 1;
+        if (isfinite(H)) {
+          const double a = (double)ct_exp((CT)(H0 - H));
+          s_ctl[2] += a < 1.0 ? a : 1.0;
+        }
+        if (!isfinite(H) || H - H0 > 1000.0) {
+          ok = 0;
+          s_flag[4] = 1;
+        } else {
+          const double lw = -H;
+          const double nl = lae<CT>(s_ctl[5], lw);
+          take = (l == 0);
+          if (!take) take = s_uleaf < (double)ct_exp((CT)(lw - nl));
+          if (take) { s_ctl[6] = sm.scal[1]; s_ctl[7] = sm.scal[2]; }
+          s_ctl[5] = nl;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      take = __shfl_sync(0xffffffffu, take, 0);
+      if (ok) {
+        if (take)
+          for (int i = lane; i < n; i += 32) sz[i] = z1[i];
+        for (int mm = 1; mm <= depth; ++mm) {
+          if ((l & ((1 << mm) - 1)) == 0) {
+            for (int i = lane; i < n; i += 32) {
+              ckp[mm * kd + i] = p1[i];
+              ckr[mm * kd + i] = srho[i];
+            }
+          }
+        }
+        for (int i = lane; i < n; i += 32) srho[i] += p1[i];
+        __syncwarp();
+        for (int mm = 1; mm <= depth && ok; ++mm) {
+          if (((l + 1) & ((1 << mm) - 1)) == 0) {
+            CT s1 = 0, s2 = 0;
+            for (int i = lane; i < n; i += 32) {
+              const CT seg = srho[i] - ckr[mm * kd + i];
+              const CT mi = minv[i % D];
+              s1 += seg * (mi * ckp[mm * kd + i]);
+              s2 += seg * (mi * p1[i]);
+            }
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            if (s1 <= 0 || s2 <= 0) ok = 0;
+          }
+        }
+      }
+      if (lane == 0) s_flag[0] = ok;
+    }
+    __syncthreads();
+    if (s_flag[0] == 0) break;       // divergence or a U-turn inside the subtree
+    if (++l < nsub) continue;
+    // ---- subtree complete: merge it into the trajectory ----
     if (warp == 0) {
       const int dir = s_flag[2];
       double* ze = dir > 0 ? zR : zL;
@@ -596,7 +607,9 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       if (lane == 0) s_flag[1] = (dl <= 0 || dr <= 0) ? 1 : 0;
     }
     __syncthreads();
-    if (s_flag[1]) break;
+    if (s_flag[1]) break;            // U-turn of the whole trajectory
+    if (++depth >= kp.max_depth) break;
+    l = 0;
   }
   if (warp == 0) {
     double* zw = kp.z + gi * (int64_t)kd;

@@ -226,126 +226,179 @@ __device__ __forceinline__ float& slot(float2 (&r)[R / 2], int s) {
 }
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// r -= h(t_{m+s}) for one component on the thread's R samples (packed pairs)
-template <int MODEL, int R>
-__device__ __forceinline__ void mixed_sub(const float* cf, float m, float2 (&r)[R / 2]) {
+// r -= h(t_{m+s}) for C components on the thread's R samples (packed pairs).
+// Sinusoids take C = 2: the two components' rotation recurrences are interleaved
+// for instruction-level parallelism, and every residual element still receives the
+// first component's update before the second's (the order of two single calls).
+// Pulses take C = 1 (the pulse kernels are issue-bound already).
+template <int MODEL, int R, int C>
+__device__ __forceinline__ void mixed_sub(const float (&cf)[C][NCF], float m, float2 (&r)[R / 2]) {
   static_assert(R % 16 == 0, "packed pulse chunks need R a multiple of 16");
-  if (MODEL == SINUSOID) {
-    float2 c, s;
-    sin_anchor(cf, m, c.x, s.x);
-    sin_anchor(cf, m + (float)(R / 2), c.y, s.y);
-    const float2 nA = f2(-cf[0]), rc = f2(cf[5]), rs = f2(cf[6]), nrs = f2(-cf[6]);
+  if constexpr (MODEL == SINUSOID) {
+    float2 c[C], s[C], nA[C], rc[C], rs[C], nrs[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      sin_anchor(cf[u], m, c[u].x, s[u].x);
+      sin_anchor(cf[u], m + (float)(R / 2), c[u].y, s[u].y);
+      nA[u] = f2(-cf[u][0]); rc[u] = f2(cf[u][5]); rs[u] = f2(cf[u][6]); nrs[u] = f2(-cf[u][6]);
+    }
 #pragma unroll
     for (int j = 0; j < R / 2; ++j) {
-      r[j] = __ffma2_rn(nA, c, r[j]);
-      const float2 c2 = __ffma2_rn(c, rc, __fmul2_rn(s, nrs));
-      s = __ffma2_rn(s, rc, __fmul2_rn(c, rs));
-      c = c2;
+#pragma unroll
+      for (int u = 0; u < C; ++u) r[j] = __ffma2_rn(nA[u], c[u], r[j]);
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
+        const float2 c2 = __ffma2_rn(c[u], rc[u], __fmul2_rn(s[u], nrs[u]));
+        s[u] = __ffma2_rn(s[u], rc[u], __fmul2_rn(c[u], rs[u]));
+        c[u] = c2;
+      }
     }
   } else {
-    const float2 nA = f2(-cf[0]), del = f2(cf[3]), rho = f2(cf[5]);
-    const float2 v00 = f2(dd_axpy(cf[1], cf[2], cf[3], cf[4], m));
-    if (cf[8] != 0.0f) {
+    static_assert(C == 1, "pulse components one at a time");
+    const bool coarse = cf[0][8] != 0.0f;
+    float2 nA[C], del[C], rho[C], v00[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      nA[u] = f2(-cf[u][0]); del[u] = f2(cf[u][3]); rho[u] = f2(cf[u][5]);
+      v00[u] = f2(dd_axpy(cf[u][1], cf[u][2], cf[u][3], cf[u][4], m));
+    }
+    if (coarse) {   // C == 1: direct evaluation of every sample
 #pragma unroll
       for (int i = 0; i < R / 2; ++i) {
         const float2 v = __ffma2_rn(make_float2((float)pair_sample<MODEL, R>(i, 0),
-                                                (float)pair_sample<MODEL, R>(i, 1)), del, v00);
-        r[i] = __ffma2_rn(nA, make_float2(ex2a(-v.x * v.x), ex2a(-v.y * v.y)), r[i]);
+                                                (float)pair_sample<MODEL, R>(i, 1)), del[0], v00[0]);
+        r[i] = __ffma2_rn(nA[0], make_float2(ex2a(-v.x * v.x), ex2a(-v.y * v.y)), r[i]);
       }
-    } else {
+      return;
+    }
 #pragma unroll
-      for (int p = 0; p < R / 16; ++p) {
-        const float2 v0 = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del, v00);
-        float2 g = make_float2(ex2a(-v0.x * v0.x), ex2a(-v0.y * v0.y));
-        float2 q = make_float2(ex2a(fminf(-__fmaf_rn(v0.x, cf[6], cf[7]), 64.0f)),
-                               ex2a(fminf(-__fmaf_rn(v0.y, cf[6], cf[7]), 64.0f)));
+    for (int p = 0; p < R / 16; ++p) {
+      float2 g[C], q[C];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          r[8 * p + j] = __ffma2_rn(nA, g, r[8 * p + j]);
-          g = __fmul2_rn(g, q);
-          q = __fmul2_rn(q, rho);
+      for (int u = 0; u < C; ++u) {
+        const float2 v0 = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del[u],
+                                     v00[u]);
+        g[u] = make_float2(ex2a(-v0.x * v0.x), ex2a(-v0.y * v0.y));
+        q[u] = make_float2(ex2a(fminf(-__fmaf_rn(v0.x, cf[u][6], cf[u][7]), 64.0f)),
+                           ex2a(fminf(-__fmaf_rn(v0.y, cf[u][6], cf[u][7]), 64.0f)));
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int u = 0; u < C; ++u) r[8 * p + j] = __ffma2_rn(nA[u], g[u], r[8 * p + j]);
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+          g[u] = __fmul2_rn(g[u], q[u]);
+          q[u] = __fmul2_rn(q[u], rho[u]);
         }
       }
     }
   }
 }
 
-// adjoint partial sums of one component over the thread's samples (rc = c_n r_n / sigma^2,
-// packed pairs as above)
+// adjoint partial sums of C components over the thread's samples
+// (rc = c_n r_n / sigma^2, packed pairs as above); C as in mixed_sub
 //   pulse:    s0 = sum rc g, s1 = sum rc g v, s2 = sum rc g v^2
 //   sinusoid: s0 = sum rc cos, s1 = sum rc sin, s2 = sum rc sin n, s3 = sum rc sin n^2
-template <int MODEL, int R>
-__device__ __forceinline__ void mixed_adj(const float* cf, float m, const float2 (&rc)[R / 2],
-                                          float (&o)[4]) {
-  if (MODEL == SINUSOID) {
-    float2 c, s;
+template <int MODEL, int R, int C>
+__device__ __forceinline__ void mixed_adj(const float (&cf)[C][NCF], float m,
+                                          const float2 (&rc)[R / 2], float (&o)[C][4]) {
+  if constexpr (MODEL == SINUSOID) {
     const float mh = m + (float)(R / 2);
-    sin_anchor(cf, m, c.x, s.x);
-    sin_anchor(cf, mh, c.y, s.y);
-    const float2 rcs = f2(cf[5]), rsn = f2(cf[6]), nrsn = f2(-cf[6]);
-    float2 sc = f2(0.f), u0 = f2(0.f), u1 = f2(0.f), u2 = f2(0.f);
+    float2 c[C], s[C], rcs[C], rsn[C], nrsn[C], sc[C], u0[C], u1[C], u2[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      sin_anchor(cf[u], m, c[u].x, s[u].x);
+      sin_anchor(cf[u], mh, c[u].y, s[u].y);
+      rcs[u] = f2(cf[u][5]); rsn[u] = f2(cf[u][6]); nrsn[u] = f2(-cf[u][6]);
+      sc[u] = u0[u] = u1[u] = u2[u] = f2(0.f);
+    }
 #pragma unroll
     for (int j = 0; j < R / 2; ++j) {
-      sc = __ffma2_rn(rc[j], c, sc);
-      const float2 p = __fmul2_rn(rc[j], s);
-      u0 = __fadd2_rn(u0, p);
-      u1 = __ffma2_rn(p, f2((float)j), u1);
-      u2 = __ffma2_rn(p, f2((float)(j * j)), u2);
-      const float2 c2 = __ffma2_rn(c, rcs, __fmul2_rn(s, nrsn));
-      s = __ffma2_rn(s, rcs, __fmul2_rn(c, rsn));
-      c = c2;
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
+        sc[u] = __ffma2_rn(rc[j], c[u], sc[u]);
+        const float2 p = __fmul2_rn(rc[j], s[u]);
+        u0[u] = __fadd2_rn(u0[u], p);
+        u1[u] = __ffma2_rn(p, f2((float)j), u1[u]);
+        u2[u] = __ffma2_rn(p, f2((float)(j * j)), u2[u]);
+        const float2 c2 = __ffma2_rn(c[u], rcs[u], __fmul2_rn(s[u], nrsn[u]));
+        s[u] = __ffma2_rn(s[u], rcs[u], __fmul2_rn(c[u], rsn[u]));
+        c[u] = c2;
+      }
     }
-    o[0] = sc.x + sc.y;
-    o[1] = u0.x + u0.y;
-    o[2] = __fmaf_rn(m, u0.x, u1.x) + __fmaf_rn(mh, u0.y, u1.y);
-    o[3] = __fmaf_rn(m, __fmaf_rn(m, u0.x, 2.0f * u1.x), u2.x) +
-           __fmaf_rn(mh, __fmaf_rn(mh, u0.y, 2.0f * u1.y), u2.y);
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      o[u][0] = sc[u].x + sc[u].y;
+      o[u][1] = u0[u].x + u0[u].y;
+      o[u][2] = __fmaf_rn(m, u0[u].x, u1[u].x) + __fmaf_rn(mh, u0[u].y, u1[u].y);
+      o[u][3] = __fmaf_rn(m, __fmaf_rn(m, u0[u].x, 2.0f * u1[u].x), u2[u].x) +
+                __fmaf_rn(mh, __fmaf_rn(mh, u0[u].y, 2.0f * u1[u].y), u2[u].y);
+    }
   } else {
-    const float2 del = f2(cf[3]), rho = f2(cf[5]);
-    const float2 v00 = f2(dd_axpy(cf[1], cf[2], cf[3], cf[4], m));
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    if (cf[8] != 0.0f) {
+    static_assert(C == 1, "pulse components one at a time");
+    const bool coarse = cf[0][8] != 0.0f;
+    float2 del[C], rho[C], v00[C];
+    float s0[C], s1[C], s2[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      del[u] = f2(cf[u][3]); rho[u] = f2(cf[u][5]);
+      v00[u] = f2(dd_axpy(cf[u][1], cf[u][2], cf[u][3], cf[u][4], m));
+      s0[u] = s1[u] = s2[u] = 0.f;
+    }
+    if (coarse) {   // C == 1
       float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f);
 #pragma unroll
       for (int i = 0; i < R / 2; ++i) {
         const float2 v = __ffma2_rn(make_float2((float)pair_sample<MODEL, R>(i, 0),
-                                                (float)pair_sample<MODEL, R>(i, 1)), del, v00);
+                                                (float)pair_sample<MODEL, R>(i, 1)), del[0], v00[0]);
         const float2 p = __fmul2_rn(rc[i], make_float2(ex2a(-v.x * v.x), ex2a(-v.y * v.y)));
         a0 = __fadd2_rn(a0, p);
         a1 = __ffma2_rn(p, v, a1);
         a2 = __ffma2_rn(__fmul2_rn(p, v), v, a2);
       }
-      s0 = a0.x + a0.y;
-      s1 = a1.x + a1.y;
-      s2 = a2.x + a2.y;
-    } else {
-      const float2 del2 = f2(cf[7]), twodel = f2(2.0f * cf[3]);
+      o[0][0] = a0.x + a0.y; o[0][1] = a1.x + a1.y; o[0][2] = a2.x + a2.y; o[0][3] = 0.f;
+      return;
+    }
 #pragma unroll
-      for (int p = 0; p < R / 16; ++p) {
-        const float2 v0 = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del, v00);
-        float2 g = make_float2(ex2a(-v0.x * v0.x), ex2a(-v0.y * v0.y));
-        float2 q = make_float2(ex2a(fminf(-__fmaf_rn(v0.x, cf[6], cf[7]), 64.0f)),
-                               ex2a(fminf(-__fmaf_rn(v0.y, cf[6], cf[7]), 64.0f)));
-        float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f);
+    for (int p = 0; p < R / 16; ++p) {
+      float2 v0[C], g[C], q[C], a0[C], a1[C], a2[C];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float2 pr = __fmul2_rn(rc[8 * p + j], g);
-          a0 = __fadd2_rn(a0, pr);
-          a1 = __ffma2_rn(pr, f2((float)j), a1);
-          a2 = __ffma2_rn(pr, f2((float)(j * j)), a2);
-          g = __fmul2_rn(g, q);
-          q = __fmul2_rn(q, rho);
+      for (int u = 0; u < C; ++u) {
+        v0[u] = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del[u], v00[u]);
+        g[u] = make_float2(ex2a(-v0[u].x * v0[u].x), ex2a(-v0[u].y * v0[u].y));
+        q[u] = make_float2(ex2a(fminf(-__fmaf_rn(v0[u].x, cf[u][6], cf[u][7]), 64.0f)),
+                           ex2a(fminf(-__fmaf_rn(v0[u].y, cf[u][6], cf[u][7]), 64.0f)));
+        a0[u] = a1[u] = a2[u] = f2(0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+          const float2 pr = __fmul2_rn(rc[8 * p + j], g[u]);
+          a0[u] = __fadd2_rn(a0[u], pr);
+          a1[u] = __ffma2_rn(pr, f2((float)j), a1[u]);
+          a2[u] = __ffma2_rn(pr, f2((float)(j * j)), a2[u]);
+          g[u] = __fmul2_rn(g[u], q[u]);
+          q[u] = __fmul2_rn(q[u], rho[u]);
         }
+      }
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
         // per chunk: sum p v = v0 a0 + del a1;  sum p v^2 = v0^2 a0 + 2 v0 del a1 + del^2 a2
-        const float2 c1 = __ffma2_rn(v0, a0, __fmul2_rn(del, a1));
-        const float2 c2 = __ffma2_rn(v0, __ffma2_rn(v0, a0, __fmul2_rn(twodel, a1)),
-                                     __fmul2_rn(del2, a2));
-        s0 += a0.x; s0 += a0.y;            // chunks in sample order
-        s1 += c1.x; s1 += c1.y;
-        s2 += c2.x; s2 += c2.y;
+        const float2 c1 = __ffma2_rn(v0[u], a0[u], __fmul2_rn(del[u], a1[u]));
+        const float2 c2 = __ffma2_rn(v0[u], __ffma2_rn(v0[u], a0[u],
+                                                       __fmul2_rn(f2(2.0f * cf[u][3]), a1[u])),
+                                     __fmul2_rn(f2(cf[u][7]), a2[u]));
+        s0[u] += a0[u].x; s0[u] += a0[u].y;            // chunks in sample order
+        s1[u] += c1.x; s1[u] += c1.y;
+        s2[u] += c2.x; s2[u] += c2.y;
       }
     }
-    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = 0.f;
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      o[u][0] = s0[u]; o[u][1] = s1[u]; o[u][2] = s2[u]; o[u][3] = 0.f;
+    }
   }
 }
 
@@ -1124,14 +1177,27 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
       act[1] = K >= 64 ? 0xffffffffu : (K > 32 ? ((1u << (K - 32)) - 1u) : 0u);
     }
     done += mine * (__popc(act[0]) + __popc(act[1]));
+    // active components in ascending k (sinusoids two at a time)
+    const unsigned long long act64 =
+        (unsigned long long)act[0] | ((unsigned long long)act[1] << 32);
 #pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      for (uint32_t bits = act[half]; bits; bits &= bits - 1u) {
-        const int k = (half << 5) + __ffs(bits) - 1;
-        float cf[NCF];
-        load_cf(sm.cf + k * NCF, cf);
-        mixed_sub<MODEL, R>(cf, mf, r);
+    for (unsigned long long bits = act64; bits;) {
+      const int ka = __ffsll((long long)bits) - 1;
+      bits &= bits - 1ull;
+      if constexpr (MODEL == SINUSOID) {
+        if (bits) {
+          const int kb = __ffsll((long long)bits) - 1;
+          bits &= bits - 1ull;
+          float cf[2][NCF];
+          load_cf(sm.cf + ka * NCF, cf[0]);
+          load_cf(sm.cf + kb * NCF, cf[1]);
+          mixed_sub<MODEL, R, 2>(cf, mf, r);
+          continue;
+        }
       }
+      float cf[1][NCF];
+      load_cf(sm.cf + ka * NCF, cf[0]);
+      mixed_sub<MODEL, R, 1>(cf, mf, r);
     }
     // residual energy and the adjoint weights rc = c_n r_n / sigma^2
     float so = 0.f, sn = 0.f;
@@ -1149,13 +1215,26 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     kahan_add(en_s, en_c, sn);
     if (GRAD) {
 #pragma unroll 1
-      for (int half = 0; half < 2; ++half)
-      for (uint32_t bits = act[half]; bits; bits &= bits - 1u) {
-        const int k = (half << 5) + __ffs(bits) - 1;
-        float cf[NCF], o[4];
-        load_cf(sm.cf + k * NCF, cf);
-        mixed_adj<MODEL, R>(cf, mf, r, o);
-        warp_accumulate<D>(o, lane, k, gacc);
+      for (unsigned long long bits = act64; bits;) {
+        const int ka = __ffsll((long long)bits) - 1;
+        bits &= bits - 1ull;
+        if constexpr (MODEL == SINUSOID) {
+          if (bits) {
+            const int kb = __ffsll((long long)bits) - 1;
+            bits &= bits - 1ull;
+            float cf[2][NCF], o[2][4];
+            load_cf(sm.cf + ka * NCF, cf[0]);
+            load_cf(sm.cf + kb * NCF, cf[1]);
+            mixed_adj<MODEL, R, 2>(cf, mf, r, o);
+            warp_accumulate<D>(o[0], lane, ka, gacc);
+            warp_accumulate<D>(o[1], lane, kb, gacc);
+            continue;
+          }
+        }
+        float cf[1][NCF], o[1][4];
+        load_cf(sm.cf + ka * NCF, cf[0]);
+        mixed_adj<MODEL, R, 1>(cf, mf, r, o);
+        warp_accumulate<D>(o[0], lane, ka, gacc);
       }
     }
     if (FISHER) {
