@@ -480,7 +480,10 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->D = model_dim(cfg->model);
   c->kd = cfg->kmax * c->D;
   c->Ptot = (int64_t)cfg->n_problems * cfg->particles;
-  c->T = cfg->threads ? cfg->threads : 128;   // best measured for both paths (N = 16384)
+  // default block: 128 threads; 256 for mixed-path sinusoids, whose rotation recurrence
+  // is latency-bound and gains from the extra warps per block
+  c->T = cfg->threads ? cfg->threads
+                      : ((cfg->model == TSMC_SINUSOID && cfg->precision == TSMC_MIXED) ? 256 : 128);
   c->R = cfg->samples_per_thread ? cfg->samples_per_thread : 32;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   Layout L;
