@@ -155,6 +155,15 @@ class ClockSampler:
         except OSError:
             self.p = None
 
+    def wait_first(self, timeout_s: float = 10.0):
+        """Returns once nvidia-smi has written its first sample (its start-up, which
+        initialises NVML on the device, stays outside the timed region)."""
+        t0 = time.perf_counter()
+        while self.p is not None and time.perf_counter() - t0 < timeout_s:
+            if os.path.getsize(self.f.name) > 0 or self.p.poll() is not None:
+                return
+            time.sleep(0.02)
+
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -316,6 +325,7 @@ def run_gpu(a):
     ctx.counters(reset=True)
     ctx.profile_read(reset=True)
     clocks = ClockSampler(local, a.clock_ms, a.clock_fields)
+    clocks.wait_first()
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
