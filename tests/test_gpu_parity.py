@@ -34,6 +34,13 @@ CASES = [
     ("pulse", 100, 4, 0, 16),
     ("sinusoid", 9000, 5, 0, 24),
     ("sinusoid", 6000, 4, 2500, 16),
+    # ragged tails at every alignment: odd N and n1 inside a thread's samples, one sample
+    # past a full segment, N below one warp range, a single sample
+    ("pulse", 1001, 7, 333, 24),
+    ("pulse", 4097, 40, 0, 16),
+    ("pulse", 37, 3, 0, 8),
+    ("pulse", 1, 2, 0, 4),
+    ("sinusoid", 777, 3, 101, 8),
 ]
 
 
@@ -205,6 +212,42 @@ def test_nuts_mixed_moves_and_stays_finite():
     np.testing.assert_allclose(ln.cpu().numpy(), ln2.cpu().numpy(), rtol=1e-12)
 
 
+def test_nuts_mixed_agrees_with_oracle():
+    """Mixed path (FP32 templates and tree control, same Philox streams) against the FP64
+    oracle: the same trees for almost every particle, and the same end points to FP32
+    accuracy where the trees agree."""
+    t = torch()
+    wl = synth.pulse_workload("t", 512, 3, 4, 64, 88)
+    ora = oracle.Oracle(wl)
+    rng = np.random.default_rng(0)
+    K = rng.integers(1, 5, 64).astype(np.int32)
+    zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+    z = np.zeros((64, 4, 3))
+    for i in range(64):
+        k = min(K[i], 3)
+        K[i] = k
+        z[i, :k] = zt[:k] + 0.05 * rng.standard_normal((k, 3))
+    beta = 0.6
+    minv = ora.metric(z, K, beta)
+    eps = 0.2
+    ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, beta)
+    ctx.set_kernel_params([eps], minv[None, :])
+    acc = t.zeros(64, dtype=t.float64, device="cuda")
+    nl = t.zeros(64, dtype=t.int32, device="cuda")
+    fl = t.zeros(64, dtype=t.int32, device="cuda")
+    ctx.nuts_move(3, 1, acc, nl, fl)
+    zg = ctx.get_population()[0].cpu().numpy()
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo = z.copy()
+    acc_o, nl_o, fl_o = ora.nuts_move(3, 1, beta, eps, minv, zo, K, lo, ln)
+    same = (nl.cpu().numpy() == nl_o) & (fl.cpu().numpy() == fl_o)
+    assert np.mean(same) >= 0.9, np.mean(same)
+    close = np.all(np.isclose(zg, zo, rtol=1e-4, atol=1e-5), axis=(1, 2))
+    assert np.mean(close[same]) >= 0.9, np.mean(close[same])
+    np.testing.assert_allclose(acc.cpu().numpy()[same], acc_o[same], rtol=1e-3, atol=1e-6)
+
+
 def test_temper_and_resample_parity():
     wl = synth.config1()
     wl.P = 512
@@ -305,6 +348,22 @@ def test_full_size_sinusoid_sampled(prec):
     idx = np.array([0, 1, 2, 3, 4, 8, 9])
     res = oracle.Oracle(wl).logl_grad(z[idx], K[idx], 0.9)
     assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[prec], 4)
+
+
+def test_full_size_assimilation_sampled():
+    """N=2^19 samples, P=16384, K_max=40: the largest configuration, with the second half
+    of the data new (tempered) and the first half assimilated; oracle on a sample."""
+    t = torch()
+    wl = synth.config4()
+    n = wl.problems[0].n
+    z, K = population(wl, 4, wl.P)
+    ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.3, n_use=n, n1=n // 2)
+    bt = dev_tensor([0.3], t.float64)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, bt, grad=True)
+    t.cuda.synchronize()
+    idx = np.r_[0, 1, np.random.default_rng(3).choice(wl.P, 6, replace=False)]
+    res = oracle.Oracle(wl, n=n, n1=n // 2).logl_grad(z[idx], K[idx], 0.3)
+    assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[capi.MIXED], 3)
 
 
 def test_autograd_function_backward():
