@@ -40,7 +40,7 @@ struct SmemPlan {
            sizeof(float) * (size_t)kd * NCF + sizeof(uint32_t) * 2 * (size_t)nwr + 32;
   }
   __host__ __device__ size_t nuts_bytes() const {
-    return sizeof(double) * (size_t)kd * (13 + 2 * (size_t)(depth + 1));   // 8-byte slots
+    return sizeof(double) * (size_t)kd * (14 + 2 * (size_t)(depth + 1));   // 8-byte slots
   }
   // eval kernel: + gradient and Gauss-Newton staging; RJ: + proposal coordinates
   __host__ __device__ size_t eval_kernel_bytes() const {
@@ -430,7 +430,8 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   const int st = (int)(sizeof(double) / sizeof(CT)) * kd;   // CT elements per slot
   CT *p1 = vc, *pL = vc + st, *pR = vc + 2 * st, *gL = vc + 3 * st, *gR = vc + 4 * st;
   CT *rho = vc + 5 * st, *srho = vc + 6 * st;
-  CT* ckp = vc + 7 * st;                       // [(depth+1)][kd] CT
+  CT* p1n = vc + 7 * st;                       // next momentum (swapped with p1 per leaf)
+  CT* ckp = vc + 8 * st;                       // [(depth+1)][kd] CT
   CT* ckr = ckp + (size_t)(sp.depth + 1) * kd;
   const double beta = kp.beta[prob];
   const double eps = kp.eps[prob];
@@ -444,9 +445,11 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   // The evaluation has one call site: iteration l = -1 evaluates the initial point,
   // then the leaves l = 0 .. 2^depth - 1 of each subtree follow in order.
   // Scalar tree state lives in shared memory and is touched by lane 0 of warp 0
-  // only; decisions reach the other lanes by shuffles, the other warps by s_flag.
+  // (s_flag[6] by lane 0 of the U-turn warp); decisions reach the other lanes by
+  // shuffles, the other warps by s_flag.
   // s_ctl: 0 H0, 1 logW, 2 sum_acc, 3 cand_lo, 4 cand_ln, 5 sub_logW, 6 sub_lo, 7 sub_ln
-  // s_flag: 0 subtree valid, 1 stop, 2 direction, 3 leaves, 4 diverged, 5 depth done
+  // s_flag: 0 leaf valid (energy), 1 stop, 2 direction, 3 leaves, 4 diverged, 5 depth done,
+  //         6 no U-turn inside the subtree
   int depth = 0, l = -1;
   double de = 0.0;
   CT de_c = 0;
@@ -518,12 +521,16 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       l = 0;
       continue;
     }
-    // ---- leaf: momentum half step, energy, multinomial choice, U-turn checks ----
+    // ---- leaf: momentum half step p' = p + eps/2 grad.  Warp 0: energy and the
+    // multinomial choice; warp uw (1, or 0 after it in a one-warp block): p' into the
+    // other momentum buffer, checkpoints and the U-turn checks of the subtrees the
+    // leaf closes.  Divergence or a U-turn ends the transition, so the U-turn state
+    // written on a divergent leaf is never read. ----
+    const int uw = blockDim.x > 32 ? 1 : 0;
     if (warp == 0) {
       CT kin = 0;
       for (int i = lane; i < n; i += 32) {
         const CT pn = p1[i] + (CT)0.5 * de_c * g1[i];
-        p1[i] = pn;
         kin += minv[i % D] * pn * pn;
       }
       kin = warp_sum(kin);
@@ -550,38 +557,44 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
       take = __shfl_sync(0xffffffffu, take, 0);
-      if (ok) {
-        if (take)
-          for (int i = lane; i < n; i += 32) sz[i] = z1[i];
-        for (int mm = 1; mm <= depth; ++mm) {
-          if ((l & ((1 << mm) - 1)) == 0) {
-            for (int i = lane; i < n; i += 32) {
-              ckp[mm * kd + i] = p1[i];
-              ckr[mm * kd + i] = srho[i];
-            }
-          }
-        }
-        for (int i = lane; i < n; i += 32) srho[i] += p1[i];
-        __syncwarp();
-        for (int mm = 1; mm <= depth && ok; ++mm) {
-          if (((l + 1) & ((1 << mm) - 1)) == 0) {
-            CT s1 = 0, s2 = 0;
-            for (int i = lane; i < n; i += 32) {
-              const CT seg = srho[i] - ckr[mm * kd + i];
-              const CT mi = minv[i % D];
-              s1 += seg * (mi * ckp[mm * kd + i]);
-              s2 += seg * (mi * p1[i]);
-            }
-            s1 = warp_sum(s1);
-            s2 = warp_sum(s2);
-            if (s1 <= 0 || s2 <= 0) ok = 0;
+      if (ok && take)
+        for (int i = lane; i < n; i += 32) sz[i] = z1[i];
+      if (lane == 0) s_flag[0] = ok;
+    }
+    if (warp == uw) {
+      for (int i = lane; i < n; i += 32) p1n[i] = p1[i] + (CT)0.5 * de_c * g1[i];
+      for (int mm = 1; mm <= depth; ++mm) {
+        if ((l & ((1 << mm) - 1)) == 0) {
+          for (int i = lane; i < n; i += 32) {
+            ckp[mm * kd + i] = p1n[i];
+            ckr[mm * kd + i] = srho[i];
           }
         }
       }
-      if (lane == 0) s_flag[0] = ok;
+      for (int i = lane; i < n; i += 32) srho[i] += p1n[i];
+      __syncwarp();
+      int uok = 1;
+      for (int mm = 1; mm <= depth && uok; ++mm) {
+        if (((l + 1) & ((1 << mm) - 1)) == 0) {
+          CT s1 = 0, s2 = 0;
+          for (int i = lane; i < n; i += 32) {
+            const CT seg = srho[i] - ckr[mm * kd + i];
+            const CT mi = minv[i % D];
+            s1 += seg * (mi * ckp[mm * kd + i]);
+            s2 += seg * (mi * p1n[i]);
+          }
+          s1 = warp_sum(s1);
+          s2 = warp_sum(s2);
+          if (s1 <= 0 || s2 <= 0) uok = 0;
+        }
+      }
+      if (lane == 0) s_flag[6] = uok;
     }
     __syncthreads();
-    if (s_flag[0] == 0) break;       // divergence or a U-turn inside the subtree
+    {
+      CT* t = p1; p1 = p1n; p1n = t;   // p1 now holds p'
+    }
+    if (s_flag[0] == 0 || s_flag[6] == 0) break;   // divergence or a U-turn inside the subtree
     if (++l < nsub) continue;
     // ---- subtree complete: merge it into the trajectory ----
     if (warp == 0) {
