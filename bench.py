@@ -459,7 +459,7 @@ def run_gpu(a):
                    "N": a.samples, "P": a.particles, "kmax": 40, "K_true": 20,
                    "precision": "mixed: FP32 templates/residuals, FP64 sums/anchors/log-weights",
                    "l2": "flushed between steps (256 MB write)",
-                   "pulse_window": "on: (component, warp range) pairs with every term < 2^-49 A "
+                   "pulse_window": "on: (component, warp range) pairs with |t - t0| > 6 w (every term < 2^-26 A) "
                                    "skipped; value counts every K_p*N component*sample",
                    "computed_fraction": (cc_eval + cc_nuts) / max(cs_eval + cs_nuts, 1),
                    "parallelism": f"{world} independent problem(s), one per GPU",

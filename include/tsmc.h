@@ -70,8 +70,8 @@ typedef struct {
                              (256 for TSMC_SINUSOID on TSMC_MIXED, else 128) */
   int32_t samples_per_thread;  /* mixed path register tile: 0 (default 32), 16 or 32 */
   int32_t pulse_window;   /* mixed pulse path: 1 skips every (component, 32-thread sample
-                             range) pair where |t - t0| > 7 w / sqrt(ln 4) throughout, i.e.
-                             all template terms < 2^-49 A (below FP32 resolution); 0 evaluates
+                             range) pair where |t - t0| > 6 w throughout, i.e. all template
+                             terms < 2^-26 A (under the FP32 resolution of A); 0 evaluates
                              every component on every sample.  FP64 path: always 0. */
   int32_t reserved;
 } tsmc_config;

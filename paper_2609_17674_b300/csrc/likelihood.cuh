@@ -103,6 +103,12 @@ constexpr int NCF = 12;
 constexpr double kLog2E = 1.4426950408889634074;
 constexpr double kCu = 1.1774100225154746910;   // sqrt(2 ln 2): u = v * kCu
 
+// Support window of the mixed pulse path: a (component, warp range) pair is skipped when
+// |v| > kSupportV on the whole range, i.e. |t - t0| > 6 widths, where every term is below
+// 2^-26 A (under the FP32 resolution of the amplitude, and far under the ~50 eps32
+// relative error of the template recurrence).
+constexpr float kSupportV = 5.1f;   // 6 sqrt(log2(e) / 2) = 5.096
+
 // pulse: v = (t - t0) kappa, kappa = sqrt(log2(e)/2)/w, g = 2^(-v^2)
 __device__ __forceinline__ void pulse_prep(double A, double t0, double w, const ProbDev& pb,
                                            float* cf) {
@@ -774,13 +780,13 @@ __device__ __forceinline__ void pulse_prep32(float A, double t0, double w, const
   cf[6] = 2.f * d_hi;
   cf[7] = d_hi * d_hi;
   cf[8] = del > 0.5 ? 1.0f : 0.0f;   // coarse grid: evaluate every sample directly
-  // support in sample index: |v| <= 7 (beyond it 2^{-v^2} < 2^-49); a0 + n del = v
+  // support in sample index: |v| <= kSupportV; a0 + n del = v
   const float idel = __frcp_rn(d_hi);
-  cf[9] = fmaxf(floorf((-7.0f - a_hi) * idel) - 2.0f, -1.0e30f);
-  cf[10] = fminf(ceilf((7.0f - a_hi) * idel) + 2.0f, 1.0e30f);
+  cf[9] = fmaxf(floorf((-kSupportV - a_hi) * idel) - 2.0f, -1.0e30f);
+  cf[10] = fminf(ceilf((kSupportV - a_hi) * idel) + 2.0f, 1.0e30f);
 }
 
-// warp-uniform: the component has no term above 2^-49 A on samples [first, last]
+// warp-uniform: the component has no term above 2^-26 A on samples [first, last]
 // (sample indices as FP32, exact below 2^24; converted once per segment)
 __device__ __forceinline__ bool outside_support(const float* cf, float first, float last) {
   return last < cf[9] || first > cf[10];
@@ -801,8 +807,8 @@ __device__ __forceinline__ void pulse_prep_df(float A, DF t0, float w, const Pro
   cf[7] = del.hi * del.hi;
   cf[8] = del.hi > 0.5f ? 1.0f : 0.0f;
   const float idel = __frcp_rn(del.hi);
-  cf[9] = fmaxf(floorf((-7.0f - a0.hi) * idel) - 2.0f, -1.0e30f);
-  cf[10] = fminf(ceilf((7.0f - a0.hi) * idel) + 2.0f, 1.0e30f);
+  cf[9] = fmaxf(floorf((-kSupportV - a0.hi) * idel) - 2.0f, -1.0e30f);
+  cf[10] = fminf(ceilf((kSupportV - a0.hi) * idel) + 2.0f, 1.0e30f);
 }
 
 __device__ __forceinline__ void sin_prep32(float A, double f, float fd, float p0,
