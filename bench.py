@@ -208,7 +208,8 @@ def _events_ms(stream, fn):
 
 def measure_extras(stream):
     """Secondary measurements: mixed vs FP64 logL+grad throughput, SMC wall time at equal
-    error against the oracle reference, and the 64-band batched workload."""
+    error against the oracle reference, the 64-band batched workload and the paper's
+    segment experiment on its pulse example."""
     import json as _json
 
     import torch
@@ -294,6 +295,27 @@ def measure_extras(stream):
                                "logl_grad_kernel": cs5 / (ms5 * 1e-3),
                                "nuts_transition": cn / (msn * 1e-3), "nuts_ms": msn}
     ctx.close()
+    # (4) the paper's pulse example (Sec. 5.1): 10 noise-free pulses in 200 s, P=6000,
+    # alpha=0.9, mixture moves 0.6/0.2/0.2, K in [1, 10]; 20 s segments, prior-start on
+    # each against posterior-start from the previous segment
+    from paper_2609_17674_b300 import experiments
+
+    wp = synth.paper_pulse_workload(P=6000)
+    r = experiments.segment_experiment(wp, seg_seconds=20.0, precision=capi.MIXED, stream=stream)
+    ks = np.arange(wp.kmax + 1)
+    out["paper_pulse_segments"] = {
+        "workload": wp.name, "segments_s": r["segments_s"],
+        "stages_prior_start": [x["stages"] for x in r["prior"]],
+        "stages_posterior_start": [x["stages"] for x in r["posterior"]],
+        "wall_s_prior_start": [round(x["wall_s"], 3) for x in r["prior"]],
+        "wall_s_posterior_start": [round(x["wall_s"], 3) for x in r["posterior"]],
+        "logz_prior_start": [round(x["logz"], 2) for x in r["prior"]],
+        "logz_posterior_start": [round(x["logz"], 2) for x in r["posterior"]],
+        "mean_k_prior_start": [round(float(np.dot(x["k_hist"], ks)), 3) for x in r["prior"]],
+        "mean_k_posterior_start": [round(float(np.dot(x["k_hist"], ks)), 3)
+                                   for x in r["posterior"]],
+        "k_mode_all_data": [int(np.argmax(r["prior"][-1]["k_hist"])),
+                            int(np.argmax(r["posterior"][-1]["k_hist"]))]}
     return out
 
 

@@ -73,7 +73,8 @@ typedef struct {
                              range) pair where |t - t0| > 6 w throughout, i.e. all template
                              terms < 2^-26 A (under the FP32 resolution of A); 0 evaluates
                              every component on every sample.  FP64 path: always 0. */
-  int32_t reserved;
+  int32_t kmin;           /* minimum component count: K prior U{kmin..kmax} (0 <= kmin <= kmax;
+                             LINAMP: ignored, K is kmax) */
 } tsmc_config;
 
 /* Workspace size for a configuration and per-problem sample capacities
@@ -101,7 +102,7 @@ tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, i
 /* LINAMP only: fixed (t0, w) per component, host [kmax][2]. */
 tsmc_status tsmc_set_fixed_components(void* ctx, const double* tw_host);
 
-/* Prior start (Sec. 4 step 1): K ~ U{0..kmax}, z ~ logistic (theta from its prior);
+/* Prior start (Sec. 4 step 1): K ~ U{kmin..kmax}, z ~ logistic (theta from its prior);
  * beta = 0, log Z = 0, step size eps_0 = 0.5 (kmax D)^(-1/4), unit metric. */
 tsmc_status tsmc_init_population(void* ctx);
 

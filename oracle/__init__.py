@@ -33,7 +33,8 @@ def build(force: bool = False) -> str:
 
 class Cfg(C.Structure):
     _fields_ = [
-        ("model", C.c_int32), ("D", C.c_int32), ("kmax", C.c_int32), ("n_mut", C.c_int32),
+        ("model", C.c_int32), ("D", C.c_int32), ("kmax", C.c_int32), ("kmin", C.c_int32),
+        ("n_mut", C.c_int32),
         ("max_depth", C.c_int32), ("schedule", C.c_int32), ("alpha", C.c_double),
         ("p_nuts", C.c_double), ("p_birth", C.c_double), ("p_death", C.c_double),
         ("lo", C.c_double * 4), ("hi", C.c_double * 4), ("logmask", C.c_uint32),
@@ -88,7 +89,7 @@ class Oracle:
         self.d = np.ascontiguousarray(pr.d[: (n or pr.n)], dtype=np.float64)
         self.fixed = (np.ascontiguousarray(wl.fixed_tw, dtype=np.float64)
                       if wl.fixed_tw is not None else None)
-        self.cfg = Cfg(model=wl.model, D=wl.D, kmax=wl.kmax, n_mut=wl.n_mut,
+        self.cfg = Cfg(model=wl.model, D=wl.D, kmax=wl.kmax, kmin=wl.kmin, n_mut=wl.n_mut,
                        max_depth=wl.max_depth, schedule=wl.schedule, alpha=wl.alpha,
                        p_nuts=wl.p_nuts, p_birth=wl.p_birth, p_death=wl.p_death,
                        lo=(C.c_double * 4)(*lo), hi=(C.c_double * 4)(*hi), logmask=wl.logmask,

@@ -236,7 +236,7 @@ void orc_logl_grad_batch(const orc_cfg* c, const orc_data* dat, const double* z,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Population initialisation (prior start): K ~ U{0..kmax}, each coordinate   */
+/* Population initialisation (prior start): K ~ U{kmin..kmax}, each coordinate*/
 /* z = logit(u) (so theta ~ its uniform / log-uniform prior); LINAMP: K fixed */
 /* at kmax and A = amp_mean + amp_sd * normal.                                */
 /* ------------------------------------------------------------------------- */
@@ -254,7 +254,7 @@ void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z
       continue;
     }
     draw(c, problem, i, 0, 0, ORC_PU_INIT, 0, w);
-    int32_t k = (int32_t)floor(orc_u01(w[0]) * (double)(c->kmax + 1));
+    int32_t k = c->kmin + (int32_t)floor(orc_u01(w[0]) * (double)(c->kmax - c->kmin + 1));
     if (k > c->kmax) k = c->kmax;
     K[i] = k;
     for (int j = 0; j < k * D; ++j) {
@@ -274,8 +274,8 @@ void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z
 /*   death: dL = -sum_n c_n (r_n h_n + h_n^2/2)/sigma^2                         */
 /* log alpha_birth = dL + log p(K+1) - log p(K) + log p_death - log p_birth,   */
 /* log alpha_death = dL + log p(K-1) - log p(K) + log p_birth - log p_death;   */
-/* p(K) uniform on {0..kmax} so the K-prior terms vanish inside the support.   */
-/* Birth at kmax and death at 0 are rejected.  Acceptance iff log u < log a.   */
+/* p(K) uniform on {kmin..kmax} so the K-prior terms vanish inside the support.*/
+/* Birth at kmax and death at kmin are rejected.  Acceptance iff log u < log a.*/
 /* ------------------------------------------------------------------------- */
 void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
                  int32_t round, double beta, int32_t P, double* z, int32_t* K,
@@ -300,7 +300,7 @@ void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t
     }
     int32_t k = K[i];
     if (birth && k >= c->kmax) { outcome[i] = -1; continue; }
-    if (!birth && k <= 0) { outcome[i] = -2; continue; }
+    if (!birth && k <= c->kmin) { outcome[i] = -2; continue; }
     /* the component that is added or removed, in theta space */
     double th_new[4], th_all[ORC_MAXKD], tmp;
     int32_t j = 0;

@@ -38,6 +38,7 @@ typedef struct {
   int32_t model;          /* ORC_PULSE / ORC_SINUSOID / ORC_PULSE_LINAMP */
   int32_t D;              /* parameters per component: 3 / 4 / 1 */
   int32_t kmax;           /* maximum component count (fixed K for LINAMP) */
+  int32_t kmin;           /* minimum component count of the K prior (0 <= kmin <= kmax) */
   int32_t n_mut;          /* mutation rounds per stage */
   int32_t max_depth;      /* NUTS maximum tree depth */
   int32_t schedule;       /* ORC_SCHED_ROUNDS or ORC_SCHED_MIXTURE */

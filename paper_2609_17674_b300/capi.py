@@ -63,7 +63,7 @@ class Config(C.Structure):
         ("p_nuts", C.c_double), ("p_birth", C.c_double), ("p_death", C.c_double),
         ("amp_mean", C.c_double), ("amp_sd", C.c_double), ("seed", C.c_uint64),
         ("threads", C.c_int32), ("samples_per_thread", C.c_int32),
-        ("pulse_window", C.c_int32), ("reserved", C.c_int32),
+        ("pulse_window", C.c_int32), ("kmin", C.c_int32),
     ]
 
 

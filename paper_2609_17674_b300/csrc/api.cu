@@ -97,6 +97,7 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (!cfg) return TSMC_EINVAL;
   if (cfg->model < 0 || cfg->model > 2 || cfg->precision < 0 || cfg->precision > 1) return TSMC_EINVAL;
   if (cfg->n_problems <= 0 || cfg->particles <= 0 || cfg->kmax < 1 || cfg->kmax > kMaxK) return TSMC_EINVAL;
+  if (cfg->kmin < 0 || cfg->kmin > cfg->kmax) return TSMC_EINVAL;
   if (cfg->max_depth < 1 || cfg->max_depth > kMaxDepth || cfg->n_mut < 0) return TSMC_EINVAL;
   if (!(cfg->alpha > 0.0 && cfg->alpha <= 1.0)) return TSMC_EINVAL;
   if (cfg->schedule == TSMC_SCHED_ROUNDS && !(cfg->p_birth > 0.0 && cfg->p_death > 0.0)) return TSMC_EINVAL;
@@ -152,6 +153,7 @@ KParams kparams(Ctx* c) {
   kp.n_problems = c->cfg.n_problems;
   kp.P = c->cfg.particles;
   kp.kmax = c->cfg.kmax;
+  kp.kmin = c->cfg.kmin;
   kp.D = c->D;
   kp.model = c->cfg.model;
   kp.schedule = c->cfg.schedule;

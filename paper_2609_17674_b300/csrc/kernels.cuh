@@ -11,7 +11,7 @@ namespace tsmc {
 // Everything a population kernel needs, passed by value.
 struct KParams {
   const ProbDev* probs;
-  int32_t n_problems, P, kmax, D, model, schedule, max_depth, n_mut;
+  int32_t n_problems, P, kmax, kmin, D, model, schedule, max_depth, n_mut;
   double p_nuts, p_birth, p_death;
   PriorArgs pa;
   uint64_t seed;
@@ -158,7 +158,7 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
     return;
   }
   Rand4 w = draw(kp.seed, prob, li, 0, 0, PU_INIT, 0);
-  int k = (int)floor(__dmul_rn(u01(w.w[0]), (double)(kp.kmax + 1)));
+  int k = kp.kmin + (int)floor(__dmul_rn(u01(w.w[0]), (double)(kp.kmax - kp.kmin + 1)));
   if (k > kp.kmax) k = kp.kmax;
   kp.K[gi] = k;
   for (int j = 0; j < k * kp.D; ++j) {
@@ -204,7 +204,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
     int out = 0;
     if (active) {
       if (birth && K >= kp.kmax) out = -1;
-      else if (!birth && K <= 0) out = -2;
+      else if (!birth && K <= kp.kmin) out = -2;
       else move = birth ? 1 : 2;
     }
     if (move == 1) {

@@ -16,7 +16,7 @@ from .synth import Workload
 def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
                 samples_per_thread: int = 0, pulse_window: int = 1) -> capi.Config:
     return capi.Config(model=wl.model, precision=precision, schedule=wl.schedule,
-                       n_problems=len(wl.problems), particles=wl.P, kmax=wl.kmax,
+                       n_problems=len(wl.problems), particles=wl.P, kmax=wl.kmax, kmin=wl.kmin,
                        n_mut=wl.n_mut, max_depth=wl.max_depth, alpha=wl.alpha, p_nuts=wl.p_nuts,
                        p_birth=wl.p_birth, p_death=wl.p_death, amp_mean=wl.amp_mean,
                        amp_sd=wl.amp_sd, seed=wl.seed, threads=threads,
@@ -48,16 +48,15 @@ def run_smc(ctx: capi.Context, max_stages: int = 500, stage0: int = 0, use_graph
     if init_prior:
         ctx.init_population()
     betas, logzs, esss = [], [], []
-    s = 0
     for s in range(max_stages):
         b, lz, e = ctx.run_stage(stage0 + s, use_graph)
         betas.append(b)
         logzs.append(lz)
         esss.append(e)
         if np.all(b >= 1.0):
-            s += 1
             break
-    return dict(n_stages=s, beta=np.array(betas), logz=np.array(logzs), ess=np.array(esss))
+    return dict(n_stages=len(betas), beta=np.array(betas), logz=np.array(logzs),
+                ess=np.array(esss))
 
 
 class LoglGrad:

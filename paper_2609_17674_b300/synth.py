@@ -68,6 +68,7 @@ class Workload:
     amp_mean: float = 1.0
     amp_sd: float = 1.0
     fixed_tw: Optional[np.ndarray] = None   # LINAMP: [kmax][2]
+    kmin: int = 0             # K prior U{kmin..kmax}
 
     @property
     def D(self) -> int:
@@ -176,6 +177,33 @@ def config4(seed=1004, P=16384, n_full=1 << 19) -> Workload:
                     problems=[pr], lo=PULSE_LO, hi=PULSE_HI, logmask=PULSE_LOGMASK, seed=seed)
 
 
+# The paper's own pulse example (Sec. 5.1): 10 Gaussian pulses in 200 s of noise-free data,
+# uniform priors on (A, mu, width) that also serve as the birth proposal, K in [1, 10],
+# 6000 particles, alpha = 0.9, mixture moves NUTS / birth / death = 0.6 / 0.2 / 0.2, and data
+# arriving in segments 20 s longer each time.  Not given there (readings): 10 samples per
+# second, a likelihood sigma of 0.05, A in [0.5, 2], width in [1, 6] s, and the injected
+# values below (one pulse near 150 s, as in its segment-count discussion).
+PAPER_PULSE_LO = (0.5, 0.0, 1.0, 0.0)
+PAPER_PULSE_HI = (2.0, 200.0, 6.0, 0.0)
+PAPER_PULSE_MU = (14.0, 31.0, 47.0, 63.0, 79.0, 96.0, 112.0, 127.0, 151.0, 178.0)
+
+
+def paper_pulse_workload(P=6000, seed=2001, rate=10.0, sigma=0.05, n_mut=5) -> Workload:
+    """Noise-free 10-pulse signal on t_n = n / rate, n < 200 rate."""
+    rng = _rng(seed)
+    k = len(PAPER_PULSE_MU)
+    A = PAPER_PULSE_LO[0] + (PAPER_PULSE_HI[0] - PAPER_PULSE_LO[0]) * rng.random(k)
+    w = 1.5 + 3.0 * rng.random(k)
+    truth = np.stack([A, np.array(PAPER_PULSE_MU), w], axis=1)
+    n = int(round(200.0 * rate))
+    t = np.arange(n, dtype=np.float64) / rate
+    pr = Problem(d=_pulse_signal(t, truth), t_origin=0.0, dt=1.0 / rate, sigma=sigma, truth=truth)
+    return Workload(name=f"paper_pulses_200s_p{P}", model=PULSE, kmax=k, P=P, problems=[pr],
+                    lo=PAPER_PULSE_LO, hi=PAPER_PULSE_HI, logmask=0, n_mut=n_mut, max_depth=6,
+                    alpha=0.9, p_nuts=0.6, p_birth=0.2, p_death=0.2, schedule=SCHED_MIXTURE,
+                    seed=seed, kmin=1)
+
+
 def config5(seed=1005, n_bands=64, P=2048, log2n=(14, 18)) -> Workload:
     """64 independent GB bands with disjoint 5 uHz windows, N_b = round(2^U[14,18])."""
     rng = _rng(seed)
@@ -210,10 +238,10 @@ def _logit(u):
 
 
 def prior_population(wl: Workload, seed: int, P_total: Optional[int] = None):
-    """K ~ U{0..kmax}; every coordinate z ~ logistic (theta ~ its prior)."""
+    """K ~ U{kmin..kmax}; every coordinate z ~ logistic (theta ~ its prior)."""
     rng = _rng(seed)
     P_total = P_total or wl.P * len(wl.problems)
-    K = rng.integers(0, wl.kmax + 1, size=P_total).astype(np.int32)
+    K = rng.integers(wl.kmin, wl.kmax + 1, size=P_total).astype(np.int32)
     u = rng.random((P_total, wl.kmax, wl.D)).clip(1e-12, 1 - 1e-12)
     z = _logit(u)
     z[np.arange(wl.kmax)[None, :] >= K[:, None]] = 0.0

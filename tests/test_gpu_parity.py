@@ -103,9 +103,11 @@ def test_fisher_parity(prec, model):
                                rtol=1e-10 if prec == capi.FP64 else 1e-4)
 
 
-def test_init_population_matches_oracle():
+@pytest.mark.parametrize("kmin", [0, 1])
+def test_init_population_matches_oracle(kmin):
     wl = synth.config1()
     wl.P = 300
+    wl.kmin = kmin
     ctx = sampler.open_context(wl, capi.FP64)
     ctx.init_population()
     z, K, lo, ln = ctx.get_population()
@@ -116,11 +118,15 @@ def test_init_population_matches_oracle():
     np.testing.assert_allclose(ln.cpu().numpy(), res["ll_new"], rtol=1e-12)
 
 
-@pytest.mark.parametrize("n1", [0, 700])
-def test_rj_move_parity_fp64(n1):
+@pytest.mark.parametrize("n1,kmin", [(0, 0), (700, 0), (0, 2)])
+def test_rj_move_parity_fp64(n1, kmin):
     t = torch()
     wl = synth.pulse_workload("t", 1500, 3, 6, 200, 77)
-    z, K = population(wl, 13, 200)
+    wl.kmin = kmin
+    z, K = population(wl, 13, 200, include_edges=kmin == 0)
+    if kmin:
+        K[:40] = kmin          # deaths proposed at the floor are rejected
+        z[:40, kmin:] = 0.0
     ora = oracle.Oracle(wl, n=1500, n1=n1)
     beta = 0.45
     ctx, zd, Kd = context_with_population(wl, capi.FP64, z, K, beta, n_use=1500, n1=n1)
@@ -138,6 +144,9 @@ def test_rj_move_parity_fp64(n1):
     np.testing.assert_allclose(lng.cpu().numpy(), ln, rtol=1e-10)
     np.testing.assert_allclose(log_.cpu().numpy(), lo, rtol=1e-10, atol=1e-9)
     assert set(np.unique(out_o)) >= {1, 2, -1} or len(np.unique(out_o)) >= 3
+    assert Kg.cpu().numpy().min() >= kmin
+    if kmin:
+        assert np.any(out_o == -2)
 
 
 def test_rj_move_mixed_agrees():

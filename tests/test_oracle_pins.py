@@ -261,6 +261,40 @@ def test_rj_converges_to_k_prior_at_beta_zero():
     assert stats.kstest(zz, "logistic").pvalue > 1e-3
 
 
+def test_rj_with_lower_bound_keeps_k_prior_at_beta_zero():
+    """K prior U{kmin..kmax} (the paper's pulse example uses [1, 10]): started at K = kmin,
+    birth/death at beta = 0 reaches the uniform prior on {kmin..kmax} and never leaves it;
+    every death proposed at K = kmin is rejected (outcome -2)."""
+    wl = synth.pulse_workload("t", 8, 1, 5, 1, 1)
+    wl.kmin = 2
+    o = oracle.Oracle(wl)
+    P = 4000
+    z = np.zeros((P, 5, 3))
+    K = np.full(P, 2, np.int32)
+    u = synth._rng(5).random((P, 2, 3))
+    z[:, :2] = np.log(u) - np.log1p(-u)
+    lo, ln = np.zeros(P), np.zeros(P)
+    rejected_at_floor = 0
+    for rnd in range(120):
+        k_before = K.copy()
+        out = o.rj_move(rnd // 16, rnd % 16, 0.0, z, K, lo, ln)
+        assert K.min() >= 2
+        rejected_at_floor += int(np.sum((k_before == 2) & (out == -2)))
+        assert np.all(out[(k_before == 2) & (K < 2)] == -2)
+    assert rejected_at_floor > 0
+    counts = np.bincount(K, minlength=6)[2:]
+    assert stats.chisquare(counts).pvalue > 1e-3
+
+
+def test_init_population_with_lower_bound():
+    wl = synth.config1()
+    wl.kmin = 1
+    z, K = oracle.Oracle(wl).init_population(20000)
+    assert K.min() == 1 and K.max() == 10
+    assert stats.chisquare(np.bincount(K, minlength=11)[1:]).pvalue > 1e-3
+    assert np.all(z[np.arange(10)[None, :] >= K[:, None]] == 0.0)
+
+
 def _toy_kposterior_workload(P, seed):
     rng = synth._rng(99)
     n = 64
