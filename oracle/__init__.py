@@ -34,6 +34,7 @@ def build(force: bool = False) -> str:
 class Cfg(C.Structure):
     _fields_ = [
         ("model", C.c_int32), ("D", C.c_int32), ("kmax", C.c_int32), ("kmin", C.c_int32),
+        ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
         ("n_mut", C.c_int32),
         ("max_depth", C.c_int32), ("schedule", C.c_int32), ("alpha", C.c_double),
         ("p_nuts", C.c_double), ("p_birth", C.c_double), ("p_death", C.c_double),
@@ -41,6 +42,17 @@ class Cfg(C.Structure):
         ("amp_mean", C.c_double), ("amp_sd", C.c_double), ("fixed_tw", C.c_void_p),
         ("seed", C.c_uint64),
     ]
+
+
+KDE_M = 256
+
+
+class Kde(C.Structure):
+    """Population birth proposal: centres [m][D] and bandwidths in z coordinates."""
+    _fields_ = [("m", C.c_int32), ("h", C.c_double * 4), ("c", C.c_double * (KDE_M * 4))]
+
+    def centres(self, D):
+        return np.ctypeslib.as_array(self.c)[: self.m * D].reshape(self.m, D).copy()
 
 
 class Data(C.Structure):
@@ -59,6 +71,10 @@ def lib():
             "orc_logl_grad_batch": (None, [P, P, P, P, I32, D, P, P, P, P, P, P]),
             "orc_init_population": (None, [P, I32, I32, P, P]),
             "orc_rj_move": (None, [P, P, I32, I32, I32, D, I32, P, P, P, P, P]),
+            "orc_rj_move_q": (None, [P, P, I32, I32, I32, D, I32, P, P, P, P, P, P]),
+            "orc_kde_build": (None, [P, I32, I32, I32, P, P, P]),
+            "orc_kde_logq": (D, [P, P, P]),
+            "orc_log_prior_z": (D, [P, P]),
             "orc_nuts_move": (None, [P, P, I32, I32, I32, D, D, P, I32, P, P, P, P, P, P, P]),
             "orc_leapfrog": (None, [P, P, I32, D, D, P, P, P, P, P]),
             "orc_temper": (None, [I32, P, D, D, P, P, P, P]),
@@ -89,7 +105,9 @@ class Oracle:
         self.d = np.ascontiguousarray(pr.d[: (n or pr.n)], dtype=np.float64)
         self.fixed = (np.ascontiguousarray(wl.fixed_tw, dtype=np.float64)
                       if wl.fixed_tw is not None else None)
-        self.cfg = Cfg(model=wl.model, D=wl.D, kmax=wl.kmax, kmin=wl.kmin, n_mut=wl.n_mut,
+        self.cfg = Cfg(model=wl.model, D=wl.D, kmax=wl.kmax, kmin=wl.kmin,
+                       birth_proposal=wl.birth_proposal,
+                       birth_prior_weight=wl.birth_prior_weight, n_mut=wl.n_mut,
                        max_depth=wl.max_depth, schedule=wl.schedule, alpha=wl.alpha,
                        p_nuts=wl.p_nuts, p_birth=wl.p_birth, p_death=wl.p_death,
                        lo=(C.c_double * 4)(*lo), hi=(C.c_double * 4)(*hi), logmask=wl.logmask,
@@ -126,12 +144,29 @@ class Oracle:
         self.L.orc_init_population(C.byref(self.cfg), self.b, P, _p(z), _p(K))
         return z, K
 
-    def rj_move(self, stage, rnd, beta, z, K, ll_old, ll_new):
+    def rj_move(self, stage, rnd, beta, z, K, ll_old, ll_new, kde=None):
         P = K.shape[0]
         out = np.zeros(P, dtype=np.int32)
-        self.L.orc_rj_move(C.byref(self.cfg), C.byref(self.data), self.b, stage, rnd, beta, P,
-                           _p(z), _p(K), _p(ll_old), _p(ll_new), _p(out))
+        self.L.orc_rj_move_q(C.byref(self.cfg), C.byref(self.data), self.b, stage, rnd, beta, P,
+                             _p(z), _p(K), _p(ll_old), _p(ll_new), _p(out),
+                             C.byref(kde) if kde is not None else None)
         return out
+
+    def kde_build(self, z, K, stage):
+        kde = Kde()
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        K = np.ascontiguousarray(K, dtype=np.int32)
+        self.L.orc_kde_build(C.byref(self.cfg), self.b, stage, K.shape[0], _p(z), _p(K),
+                             C.byref(kde))
+        return kde
+
+    def kde_logq(self, kde, z):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        return self.L.orc_kde_logq(C.byref(self.cfg), C.byref(kde), _p(z))
+
+    def log_prior_z(self, z):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        return self.L.orc_log_prior_z(C.byref(self.cfg), _p(z))
 
     def nuts_move(self, stage, rnd, beta, eps, minv, z, K, ll_old, ll_new):
         P = K.shape[0]

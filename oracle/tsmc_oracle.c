@@ -277,11 +277,12 @@ void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z
 /* p(K) uniform on {kmin..kmax} so the K-prior terms vanish inside the support.*/
 /* Birth at kmax and death at kmin are rejected.  Acceptance iff log u < log a.*/
 /* ------------------------------------------------------------------------- */
-void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
-                 int32_t round, double beta, int32_t P, double* z, int32_t* K,
-                 double* ll_old, double* ll_new, int32_t* outcome) {
+void orc_rj_move_q(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
+                   int32_t round, double beta, int32_t P, double* z, int32_t* K,
+                   double* ll_old, double* ll_new, int32_t* outcome, const orc_kde* kde) {
   const int D = c->D;
   const int64_t stride = (int64_t)c->kmax * D;
+  const int use_q = kde != NULL && c->birth_proposal == 1;
   for (int32_t i = 0; i < P; ++i) {
     outcome[i] = 0;
     if (c->model == ORC_PULSE_LINAMP) continue;
@@ -307,13 +308,23 @@ void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t
     for (int q = 0; q < k * D; ++q) orc_z_to_theta(c, q % D, zi[q], &th_all[q], &tmp);
     double znew[4];
     if (birth) {
-      uint64_t pw[4];
+      uint64_t pw[4], mw[4];
       draw(c, problem, i, stage, round, ORC_PU_RJPARAM, 0, pw);
-      for (int d = 0; d < D; ++d) {
-        double u = orc_u01(pw[d]);
-        znew[d] = log(u) - log1p(-u);
-        orc_z_to_theta(c, d, znew[d], &th_new[d], &tmp);
+      draw(c, problem, i, stage, round, ORC_PU_RJPARAM, 2, mw);
+      if (use_q && kde->m > 0 && orc_u01(mw[0]) >= c->birth_prior_weight) {
+        /* from the population mixture: centre q, then a normal step of width h */
+        int32_t q = (int32_t)floor(orc_u01(mw[1]) * (double)kde->m);
+        if (q >= kde->m) q = kde->m - 1;
+        for (int d = 0; d < D; ++d)
+          znew[d] = kde->c[q * D + d] +
+                    kde->h[d] * draw_normal(c, problem, i, stage, round, ORC_PU_RJPARAM, 4 + d);
+      } else {
+        for (int d = 0; d < D; ++d) {
+          double u = orc_u01(pw[d]);
+          znew[d] = log(u) - log1p(-u);
+        }
       }
+      for (int d = 0; d < D; ++d) orc_z_to_theta(c, d, znew[d], &th_new[d], &tmp);
     } else {
       j = (int32_t)floor(orc_u01(w[2]) * (double)k);
       if (j >= k) j = k - 1;
@@ -334,6 +345,10 @@ void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t
     double dl = d_old + beta * d_new;
     double log_alpha = birth ? dl + log(c->p_death) - log(c->p_birth)
                              : dl + log(c->p_birth) - log(c->p_death);
+    if (use_q) {   /* the proposal no longer cancels the prior of the component */
+      if (birth) log_alpha += orc_log_prior_z(c, znew) - orc_kde_logq(c, kde, znew);
+      else log_alpha += orc_kde_logq(c, kde, zi + j * D) - orc_log_prior_z(c, zi + j * D);
+    }
     double u = orc_u01(w[1]);
     if (log(u) < log_alpha) {
       if (birth) {
@@ -353,6 +368,95 @@ void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t
     } else {
       outcome[i] = birth ? -1 : -2;
     }
+  }
+}
+
+void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
+                 int32_t round, double beta, int32_t P, double* z, int32_t* K,
+                 double* ll_old, double* ll_new, int32_t* outcome) {
+  orc_rj_move_q(c, dat, problem, stage, round, beta, P, z, K, ll_old, ll_new, outcome, NULL);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Population birth proposal (Sec. 6: the particles of each stage approximate  */
+/* its tempered distribution, which can serve as the birth proposal).         */
+/* In z coordinates every parameter's prior is the standard logistic density, */
+/*   log prior_z(z) = sum_d ( -|z_d| - 2 log(1 + e^{-|z_d|}) ).                */
+/* The proposal mixes it with a Gaussian kernel density estimate:             */
+/*   q(z) = eps prior_z(z) + (1 - eps)/m sum_i prod_d N(z_d; c_id, h_d^2),     */
+/* whose m centres are components drawn uniformly, with replacement, over all */
+/* components of the population (draw i: particle slot i of purpose KDE, the  */
+/* stage, round 0), and h_d = sd_d (4/(D+2))^(1/(D+4)) m^(-1/(D+4)) (the      */
+/* normal-reference rule, sd_d the sample deviation of the centres; at least  */
+/* 1e-3).  The weight eps keeps q positive wherever the prior is.             */
+/* ------------------------------------------------------------------------- */
+double orc_log_prior_z(const orc_cfg* c, const double* z) {
+  double s = 0.0;
+  for (int d = 0; d < c->D; ++d) {
+    const double a = fabs(z[d]);
+    s += -a - 2.0 * log1p(exp(-a));
+  }
+  return s;
+}
+
+double orc_kde_logq(const orc_cfg* c, const orc_kde* kde, const double* z) {
+  const int D = c->D;
+  const double lp = orc_log_prior_z(c, z);
+  if (kde->m == 0 || c->birth_prior_weight >= 1.0) return lp;
+  /* terms of the mixture, then log-sum-exp in index order */
+  double t[ORC_KDE_M + 1];
+  t[0] = log(c->birth_prior_weight) + lp;
+  const double lw = log((1.0 - c->birth_prior_weight) / (double)kde->m);
+  for (int i = 0; i < kde->m; ++i) {
+    double e = lw;
+    for (int d = 0; d < D; ++d) {
+      const double u = (z[d] - kde->c[i * D + d]) / kde->h[d];
+      e += -0.5 * u * u - log(kde->h[d]) - 0.5 * log(2.0 * M_PI);
+    }
+    t[i + 1] = e;
+  }
+  double mx = t[0];
+  for (int i = 1; i <= kde->m; ++i) if (t[i] > mx) mx = t[i];
+  double sum = 0.0;
+  for (int i = 0; i <= kde->m; ++i) sum += exp(t[i] - mx);
+  return mx + log(sum);
+}
+
+void orc_kde_build(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
+                   const double* z, const int32_t* K, orc_kde* kde) {
+  const int D = c->D;
+  const int64_t stride = (int64_t)c->kmax * D;
+  int64_t total = 0;
+  for (int32_t i = 0; i < P; ++i) total += K[i];
+  kde->m = 0;
+  for (int d = 0; d < 4; ++d) kde->h[d] = 1.0;
+  if (total == 0) return;
+  kde->m = ORC_KDE_M;
+  for (int32_t i = 0; i < ORC_KDE_M; ++i) {
+    uint64_t w[4];
+    draw(c, problem, (uint64_t)i, stage, 0, ORC_PU_KDE, 0, w);
+    int64_t q = (int64_t)floor(orc_u01(w[0]) * (double)total);
+    if (q >= total) q = total - 1;
+    int32_t p = 0;          /* the particle holding component number q */
+    int64_t before = 0;
+    while (before + K[p] <= q) { before += K[p]; ++p; }
+    const int64_t j = q - before;
+    for (int d = 0; d < D; ++d) kde->c[i * D + d] = z[p * stride + j * D + d];
+  }
+  const double f = pow(4.0 / (double)(D + 2), 1.0 / (double)(D + 4)) *
+                   pow((double)ORC_KDE_M, -1.0 / (double)(D + 4));
+  for (int d = 0; d < D; ++d) {
+    double mean = 0.0;
+    for (int i = 0; i < ORC_KDE_M; ++i) mean += kde->c[i * D + d];
+    mean /= (double)ORC_KDE_M;
+    double var = 0.0;
+    for (int i = 0; i < ORC_KDE_M; ++i) {
+      const double e = kde->c[i * D + d] - mean;
+      var += e * e;
+    }
+    var /= (double)(ORC_KDE_M - 1);
+    double h = sqrt(var) * f;
+    kde->h[d] = h < 1e-3 ? 1e-3 : h;
   }
 }
 
@@ -651,6 +755,8 @@ int32_t orc_smc_run(const orc_cfg* c, const orc_data* dat, int32_t problem, int3
   int32_t* nl = (int32_t*)malloc(sizeof(int32_t) * (size_t)P);
   int32_t* fl = (int32_t*)malloc(sizeof(int32_t) * (size_t)P);
   double beta = 0.0, eps = *eps_io, minv[4];
+  orc_kde* kde = (c->birth_proposal == 1 && c->model != ORC_PULSE_LINAMP)
+                     ? (orc_kde*)malloc(sizeof(orc_kde)) : NULL;
   *logz = 0.0;
   int32_t s = 0;
   for (; s < max_stages && beta < 1.0; ++s) {
@@ -670,10 +776,11 @@ int32_t orc_smc_run(const orc_cfg* c, const orc_data* dat, int32_t problem, int3
     memcpy(ll_old, lo2, sizeof(double) * (size_t)P);
     memcpy(ll_new, ln2, sizeof(double) * (size_t)P);
     orc_metric(c, dat, z, K, P, beta, minv);
+    if (kde) orc_kde_build(c, problem, stage, P, z, K, kde);
     double acc_sum = 0.0;
     int64_t acc_n = 0;
     for (int32_t r = 0; r < c->n_mut; ++r) {
-      orc_rj_move(c, dat, problem, stage, r, beta, P, z, K, ll_old, ll_new, fl);
+      orc_rj_move_q(c, dat, problem, stage, r, beta, P, z, K, ll_old, ll_new, fl, kde);
       orc_nuts_move(c, dat, problem, stage, r, beta, eps, minv, P, z, K, ll_old, ll_new, acc,
                     nl, fl);
       for (int32_t i = 0; i < P; ++i) if (nl[i] > 0) { acc_sum += acc[i]; ++acc_n; }
@@ -685,5 +792,6 @@ int32_t orc_smc_run(const orc_cfg* c, const orc_data* dat, int32_t problem, int3
   }
   *eps_io = eps;
   free(logw); free(anc); free(z2); free(K2); free(lo2); free(ln2); free(acc); free(nl); free(fl);
+  free(kde);
   return s;
 }

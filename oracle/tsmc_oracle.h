@@ -31,7 +31,7 @@ enum { ORC_SCHED_ROUNDS = 0, ORC_SCHED_MIXTURE = 1 };
 enum {
   ORC_PU_INIT = 0, ORC_PU_MOMENTUM = 1, ORC_PU_DIRECTION = 2, ORC_PU_LEAF = 3,
   ORC_PU_TOP = 4, ORC_PU_RJ = 5, ORC_PU_RJPARAM = 6, ORC_PU_RESAMPLE = 7,
-  ORC_PU_MOVETYPE = 8
+  ORC_PU_MOVETYPE = 8, ORC_PU_KDE = 9
 };
 
 typedef struct {
@@ -39,6 +39,8 @@ typedef struct {
   int32_t D;              /* parameters per component: 3 / 4 / 1 */
   int32_t kmax;           /* maximum component count (fixed K for LINAMP) */
   int32_t kmin;           /* minimum component count of the K prior (0 <= kmin <= kmax) */
+  int32_t birth_proposal; /* 0: births from the prior; 1: population mixture (orc_kde) */
+  double birth_prior_weight;      /* epsilon: prior weight of the population mixture */
   int32_t n_mut;          /* mutation rounds per stage */
   int32_t max_depth;      /* NUTS maximum tree depth */
   int32_t schedule;       /* ORC_SCHED_ROUNDS or ORC_SCHED_MIXTURE */
@@ -58,6 +60,16 @@ typedef struct {
   double t_origin, dt;    /* t_n = t_origin + n*dt */
   double sigma;           /* white-noise standard deviation */
 } orc_data;
+
+/* Population birth proposal (the paper's suggestion for future work, Sec. 6: the
+ * particles approximate each tempered distribution, so it can serve as the proposal):
+ * q(z) = eps * prior_z(z) + (1 - eps) / m * sum_i N(z; c_i, diag(h^2)) in z coordinates. */
+#define ORC_KDE_M 256
+typedef struct {
+  int32_t m;                      /* centres in use (0: the proposal is the prior) */
+  double h[4];                    /* bandwidth per parameter type */
+  double c[ORC_KDE_M * 4];        /* centres [m][D] */
+} orc_kde;
 
 void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 double orc_u01(uint64_t x);
@@ -87,6 +99,18 @@ void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z
 void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
                  int32_t round, double beta, int32_t P, double* z, int32_t* K,
                  double* ll_old, double* ll_new, int32_t* outcome);
+
+/* the same move with births proposed from q (kde != NULL and c->birth_proposal == 1) */
+void orc_rj_move_q(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
+                   int32_t round, double beta, int32_t P, double* z, int32_t* K,
+                   double* ll_old, double* ll_new, int32_t* outcome, const orc_kde* kde);
+
+/* centres: m = ORC_KDE_M components drawn uniformly (with replacement) over all
+ * components of the population; bandwidth by the normal-reference rule */
+void orc_kde_build(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
+                   const double* z, const int32_t* K, orc_kde* kde);
+double orc_log_prior_z(const orc_cfg* c, const double* z);     /* one component, D values */
+double orc_kde_logq(const orc_cfg* c, const orc_kde* kde, const double* z);
 
 /* one NUTS transition per particle with step size eps and diagonal inverse metric
  * minv[D] (per parameter type).  acc_stat[i] mean min(1,exp(H0-H)) over leaves,

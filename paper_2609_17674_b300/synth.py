@@ -69,6 +69,8 @@ class Workload:
     amp_sd: float = 1.0
     fixed_tw: Optional[np.ndarray] = None   # LINAMP: [kmax][2]
     kmin: int = 0             # K prior U{kmin..kmax}
+    birth_proposal: int = 0   # 0: births from the prior; 1: population mixture
+    birth_prior_weight: float = 0.2   # prior weight of the population mixture
 
     @property
     def D(self) -> int:

@@ -434,3 +434,87 @@ def test_eps_update_rule():
     assert L.orc_eps_update(0.1, 0.8) == pytest.approx(0.1)
     assert L.orc_eps_update(0.1, 0.3) == pytest.approx(0.1 * math.exp(-0.5))
     assert L.orc_eps_update(1.9, 1.0) == 2.0 and L.orc_eps_update(1e-4, 0.0) == 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Population birth proposal (Sec. 6 suggestion): q(z) = eps prior_z + (1 - eps) KDE
+# ---------------------------------------------------------------------------
+def _mismatched_kde(D, centre, h):
+    kde = oracle.Kde()
+    kde.m = oracle.KDE_M
+    rng = np.random.default_rng(3)
+    c = np.asarray(centre)[None, :] + 0.2 * rng.standard_normal((oracle.KDE_M, D))
+    flat = np.zeros(oracle.KDE_M * 4)
+    flat[: oracle.KDE_M * D] = c.ravel()
+    kde.c[:] = flat
+    for d in range(4):
+        kde.h[d] = h
+    return kde
+
+
+def test_population_birth_proposal_keeps_the_prior_at_beta_zero():
+    """Reversible jump with births drawn from a fixed proposal that is far from the prior
+    (centres near z = (1.5, -1, 0.5), width 0.3): at beta = 0 the chain must still leave
+    the prior invariant, K ~ U{0..5} and every coordinate standard logistic.  Dropping or
+    inverting the proposal-density ratio in either move pulls both off."""
+    wl = synth.pulse_workload("t", 8, 1, 5, 1, 1)
+    wl.birth_proposal, wl.birth_prior_weight = 1, 0.2
+    o = oracle.Oracle(wl)
+    kde = _mismatched_kde(3, (1.5, -1.0, 0.5), 0.3)
+    P = 4000
+    z, K = o.init_population(P)
+    lo, ln = np.zeros(P), np.zeros(P)
+    births = 0
+    for rnd in range(160):
+        out = o.rj_move(rnd // 16, rnd % 16, 0.0, z, K, lo, ln, kde=kde)
+        births += int(np.sum(out == 1))
+    assert births > 10000
+    assert stats.chisquare(np.bincount(K, minlength=6)).pvalue > 1e-3
+    for d in range(3):
+        zz = np.concatenate([z[i, : K[i], d] for i in range(P)])
+        assert stats.kstest(zz, "logistic").pvalue > 1e-3, d
+
+
+def test_population_proposal_is_a_normalised_density():
+    """E over the prior of q(z) / prior_z(z) is 1 (importance-sampling identity)."""
+    wl = synth.pulse_workload("t", 8, 1, 5, 1, 1)
+    wl.birth_proposal, wl.birth_prior_weight = 1, 0.2
+    o = oracle.Oracle(wl)
+    kde = _mismatched_kde(3, (0.8, -0.4, 0.2), 0.5)
+    rng = np.random.default_rng(11)
+    u = rng.random((40000, 3))
+    zs = np.log(u) - np.log1p(-u)
+    r = np.array([math.exp(o.kde_logq(kde, zz) - o.log_prior_z(zz)) for zz in zs])
+    assert abs(r.mean() - 1.0) < 4 * r.std() / math.sqrt(len(r))
+    # prior-only mixture (eps = 1) is the prior itself
+    wl.birth_prior_weight = 1.0
+    o1 = oracle.Oracle(wl)
+    assert o1.kde_logq(kde, zs[0]) == o1.log_prior_z(zs[0])
+
+
+def test_population_proposal_centres_are_uniform_over_components():
+    """Centres are components of the population, drawn uniformly over components (not
+    over particles): particle p is chosen in proportion to K_p."""
+    wl = synth.pulse_workload("t", 8, 1, 5, 50, 1)
+    wl.birth_proposal = 1
+    o = oracle.Oracle(wl)
+    rng = np.random.default_rng(2)
+    K = rng.integers(0, 6, 50).astype(np.int32)
+    z = np.zeros((50, 5, 3))
+    for p in range(50):
+        z[p, : K[p]] = p + 0.1 * np.arange(K[p])[:, None] + np.array([0.0, 0.01, 0.02])
+    counts = np.zeros(50)
+    for stage in range(40):
+        kde = o.kde_build(z, K, stage)
+        c = kde.centres(3)
+        assert kde.m == oracle.KDE_M
+        owner = np.floor(c[:, 0] + 1e-9).astype(int)
+        slot = np.round((c[:, 0] - owner) / 0.1).astype(int)
+        assert np.all(slot < K[owner])                      # a real component of that particle
+        np.testing.assert_allclose(c, z[owner, slot])
+        counts += np.bincount(owner, minlength=50)
+        assert all(kde.h[d] > 0 for d in range(3))
+    expected = counts.sum() * K / K.sum()
+    m = expected > 0
+    assert np.all(counts[~m] == 0)
+    assert stats.chisquare(counts[m], expected[m]).pvalue > 1e-3
