@@ -75,6 +75,10 @@ typedef struct {
                              every component on every sample.  FP64 path: always 0. */
   int32_t kmin;           /* minimum component count: K prior U{kmin..kmax} (0 <= kmin <= kmax;
                              LINAMP: ignored, K is kmax) */
+  int32_t birth_proposal; /* 0: births drawn from the prior (Sec. 4, the paper's method);
+                             1: from the population mixture described at
+                             tsmc_build_birth_proposal (Sec. 6 suggestion).  LINAMP: ignored */
+  double birth_prior_weight;  /* eps in (0, 1] of that mixture (used when birth_proposal = 1) */
 } tsmc_config;
 
 /* Workspace size for a configuration and per-problem sample capacities
@@ -146,6 +150,25 @@ tsmc_status tsmc_nuts_move(void* ctx, int32_t stage, int32_t round, double* acc_
  * minv_host[n_problems][D]. */
 tsmc_status tsmc_set_kernel_params(void* ctx, const double* eps_host, const double* minv_host);
 tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_host, double* minv_host);
+
+/* Population birth proposal (Sec. 6: the particles of each SMC stage approximate its
+ * tempered distribution, so that distribution can propose births).  In z coordinates
+ *   q(z) = eps prior_z(z) + (1 - eps)/m sum_i N(z; c_i, diag(h^2)),
+ * prior_z the standard logistic density per parameter, eps = birth_prior_weight, the
+ * m = 256 centres c_i components drawn uniformly (with replacement) over all components of
+ * the population, h_d = sd_d (4/(D+2))^(1/(D+4)) m^(-1/(D+4)) (normal-reference rule on the
+ * centres, at least 1e-3).  Births then carry log prior_z(z_new) - log q(z_new) and deaths
+ * log q(z_j) - log prior_z(z_j) in their acceptance.  With birth_proposal = 1,
+ * tsmc_run_stage builds it after resampling from the resampled population; this call
+ * builds it now from the context population with the given stage number in the random
+ * stream (stream-ordered; EINVAL for LINAMP or stage < 0).  Until a build, every problem's
+ * proposal is the prior. */
+tsmc_status tsmc_build_birth_proposal(void* ctx, int32_t stage);
+
+/* The proposal of one problem into host out[n]: out[0] = m (0: none built or no
+ * components), out[1..4] = h, out[5 ..] = centres [256][D] row-major.  n >= 5 + 256 D,
+ * else EINVAL.  Synchronises the context stream. */
+tsmc_status tsmc_get_birth_proposal(void* ctx, int32_t problem, double* out_host, int64_t n);
 
 /* Metric from the population (Sec. 3.2, mass matrix = Hessian of -log target):
  * minv_d = 1 / max(1e-8, mean over particles and active components of the

@@ -38,6 +38,8 @@ SIGNATURES = {
     "tsmc_nuts_move": (I32, [P, I32, I32, P, P, P]),
     "tsmc_set_kernel_params": (I32, [P, P, P]),
     "tsmc_get_kernel_params": (I32, [P, P, P]),
+    "tsmc_build_birth_proposal": (I32, [P, I32]),
+    "tsmc_get_birth_proposal": (I32, [P, I32, P, I64]),
     "tsmc_update_metric": (I32, [P]),
     "tsmc_temper_reweight_resample": (I32, [P, I32, P, P, P]),
     "tsmc_get_state": (I32, [P, P, P, P]),
@@ -64,6 +66,7 @@ class Config(C.Structure):
         ("amp_mean", C.c_double), ("amp_sd", C.c_double), ("seed", C.c_uint64),
         ("threads", C.c_int32), ("samples_per_thread", C.c_int32),
         ("pulse_window", C.c_int32), ("kmin", C.c_int32),
+        ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
     ]
 
 
@@ -213,6 +216,16 @@ class Context:
 
     def update_metric(self):
         self._check(self.L.tsmc_update_metric(self.h))
+
+    def build_birth_proposal(self, stage):
+        self._check(self.L.tsmc_build_birth_proposal(self.h, stage))
+
+    def get_birth_proposal(self, problem=0):
+        """(m, h[4], centres [m][D]) of the population birth proposal of one problem."""
+        out = np.zeros(5 + 256 * self.D)
+        self._check(self.L.tsmc_get_birth_proposal(self.h, problem, _ptr(out), out.size))
+        m = int(out[0])
+        return m, out[1:5].copy(), out[5:].reshape(256, self.D)[:m].copy()
 
     def temper_reweight_resample(self, stage):
         b, lz, e = (np.zeros(self.cfg.n_problems) for _ in range(3))

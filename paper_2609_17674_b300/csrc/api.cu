@@ -44,6 +44,8 @@ struct Ctx {
   unsigned long long* cs_count = nullptr;
   int32_t* order = nullptr;      // [Ptot] launch order of particle blocks
   int32_t* order_hist = nullptr; // [kOrderBuckets] bucket counts / offsets (scratch)
+  double* kde = nullptr;         // [n_problems][kKdeStride] population birth proposals
+  int32_t* kcum = nullptr;       // [Ptot] prefix counts of K (scratch of the proposal build)
   double nmax = 1.0;             // largest problem capacity (cost normalisation)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -90,7 +92,8 @@ struct Layout {
 
 struct Offsets {
   size_t probs, d64, d32, z, z2, K, K2, llo, llo2, lln, lln2, logw, cw, anc, acc, nleaf, flags,
-      outcome, fis, beta, logz, ess, eps, minv, stats, stage, tw, cs, order, order_hist;
+      outcome, fis, beta, logz, ess, eps, minv, stats, stage, tw, cs, order, order_hist, kde,
+      kcum;
 };
 
 tsmc_status check_cfg(const tsmc_config* cfg) {
@@ -104,6 +107,9 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->threads != 0 && (cfg->threads < 32 || cfg->threads > 256 || cfg->threads % 32)) return TSMC_EINVAL;
   if (cfg->samples_per_thread != 0 && cfg->samples_per_thread != 16 && cfg->samples_per_thread != 32) return TSMC_EINVAL;
   if (cfg->pulse_window != 0 && cfg->pulse_window != 1) return TSMC_EINVAL;
+  if (cfg->birth_proposal != 0 && cfg->birth_proposal != 1) return TSMC_EINVAL;
+  if (cfg->birth_proposal == 1 && !(cfg->birth_prior_weight > 0.0 && cfg->birth_prior_weight <= 1.0))
+    return TSMC_EINVAL;
   return TSMC_OK;
 }
 
@@ -144,6 +150,8 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.cs = L.take(sizeof(unsigned long long) * 4);   // nominal / computed x batched / NUTS
   o.order = L.take(sizeof(int32_t) * Ptot);
   o.order_hist = L.take(sizeof(int32_t) * kOrderBuckets);
+  o.kde = L.take(sizeof(double) * kKdeStride * cfg->n_problems);
+  o.kcum = L.take(sizeof(int32_t) * Ptot);
   return o;
 }
 
@@ -162,6 +170,9 @@ KParams kparams(Ctx* c) {
   kp.p_nuts = c->cfg.p_nuts;
   kp.p_birth = c->cfg.p_birth;
   kp.p_death = c->cfg.p_death;
+  kp.birth_proposal = (c->cfg.birth_proposal == 1 && c->cfg.model != TSMC_PULSE_LINAMP) ? 1 : 0;
+  kp.birth_eps = c->cfg.birth_prior_weight;
+  kp.kde = c->kde;
   kp.pa.model = c->cfg.model;
   kp.pa.amp_mean = c->cfg.amp_mean;
   kp.pa.amp_sd = c->cfg.amp_sd;
@@ -382,6 +393,17 @@ tsmc_status set_stage(Ctx* c, int stage) {
 }
 
 // mutation part of a stage: metric, n_mut rounds, step size (graph-capturable)
+// population birth proposal from the context population (stage_arg < 0: device counter)
+tsmc_status kde_launch(Ctx* c, int stage_arg) {
+  const int D = c->D;
+  const double factor = std::pow(4.0 / (double)(D + 2), 1.0 / (double)(D + 4)) *
+                        std::pow((double)kKdeM, -1.0 / (double)(D + 4));
+  pre(c, KC_OTHER);
+  k_kde_build<<<c->cfg.n_problems, 256, 0, c->stream>>>(kparams(c), c->kcum, c->kde, factor,
+                                                         stage_arg);
+  return last_launch(c, "k_kde_build");
+}
+
 tsmc_status mutation_body(Ctx* c) {
   EvalIO io{c->z, c->K, c->beta, c->llo, c->lln, nullptr, nullptr, c->fis};
   TRY(eval_launch(c, io, true, true));
@@ -389,6 +411,7 @@ tsmc_status mutation_body(Ctx* c) {
   pre(c, KC_METRIC);
   k_metric<<<np, 256, 0, c->stream>>>(c->fis, c->K, c->probs, P, c->D, c->minv);
   TRY(last_launch(c, "k_metric"));
+  if (c->cfg.birth_proposal == 1 && c->cfg.model != TSMC_PULSE_LINAMP) TRY(kde_launch(c, -1));
   for (int r = 0; r < c->cfg.n_mut; ++r) {
     if (c->cfg.model != TSMC_PULSE_LINAMP) TRY(rj_launch(c, r, c->outcome));
     TRY(nuts_launch(c, r, NutsOut{c->acc, c->nleaf, c->flags}));
@@ -521,6 +544,8 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->cs_count = reinterpret_cast<unsigned long long*>(b + o.cs);
   c->order = reinterpret_cast<int32_t*>(b + o.order);
   c->order_hist = reinterpret_cast<int32_t*>(b + o.order_hist);
+  c->kde = reinterpret_cast<double*>(b + o.kde);
+  c->kcum = reinterpret_cast<int32_t*>(b + o.kcum);
   for (int p = 0; p < cfg->n_problems; ++p) c->nmax = std::max(c->nmax, (double)cap[p]);
   c->cap.assign(cap, cap + cfg->n_problems);
   c->off.resize(cfg->n_problems);
@@ -741,6 +766,29 @@ tsmc_status tsmc_set_kernel_params(void* ctx, const double* eps_h, const double*
     TRY_CUDA(c, cudaMemcpyAsync(c->minv, m.data(), sizeof(double) * 4 * np, cudaMemcpyHostToDevice, c->stream));
   }
   return sync_stream(c);
+}
+
+tsmc_status tsmc_build_birth_proposal(void* ctx, int32_t stage) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return TSMC_EINVAL;
+  if (c->cfg.model == TSMC_PULSE_LINAMP || stage < 0)
+    return fail(c, TSMC_EINVAL, "no birth proposal for this model or stage");
+  return kde_launch(c, stage);
+}
+
+tsmc_status tsmc_get_birth_proposal(void* ctx, int32_t problem, double* out_h, int64_t n) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return TSMC_EINVAL;
+  if (!out_h || problem < 0 || problem >= c->cfg.n_problems || n < 5 + (int64_t)kKdeM * c->D)
+    return fail(c, TSMC_EINVAL, "bad problem or output size");
+  std::vector<double> v(kKdeStride);
+  TRY_CUDA(c, cudaMemcpyAsync(v.data(), c->kde + (int64_t)problem * kKdeStride,
+                              sizeof(double) * kKdeStride, cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_stream(c));
+  out_h[0] = v[0];
+  for (int d = 0; d < 4; ++d) out_h[1 + d] = v[1 + d];
+  for (int64_t i = 0; i < (int64_t)kKdeM * c->D; ++i) out_h[5 + i] = v[8 + i];
+  return TSMC_OK;
 }
 
 tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_h, double* minv_h) {

@@ -15,8 +15,13 @@ enum Model { PULSE = 0, SINUSOID = 1, PULSE_LINAMP = 2 };
 enum Prec { FP64 = 0, MIXED = 1 };
 enum Purpose {
   PU_INIT = 0, PU_MOMENTUM = 1, PU_DIRECTION = 2, PU_LEAF = 3, PU_TOP = 4,
-  PU_RJ = 5, PU_RJPARAM = 6, PU_RESAMPLE = 7, PU_MOVETYPE = 8
+  PU_RJ = 5, PU_RJPARAM = 6, PU_RESAMPLE = 7, PU_MOVETYPE = 8, PU_KDE = 9
 };
+
+// Population birth proposal per problem (doubles): [0] m centres, [1..4] bandwidth h_d,
+// [8 ..] centres [m][D] in z coordinates
+constexpr int kKdeM = 256;
+constexpr int kKdeStride = 8 + kKdeM * 4;
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter layout of the

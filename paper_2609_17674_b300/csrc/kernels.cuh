@@ -13,6 +13,9 @@ struct KParams {
   const ProbDev* probs;
   int32_t n_problems, P, kmax, kmin, D, model, schedule, max_depth, n_mut;
   double p_nuts, p_birth, p_death;
+  int32_t birth_proposal;    // 0: births from the prior; 1: population mixture (kde)
+  double birth_eps;          // prior weight of the population mixture
+  const double* kde;         // [n_problems][kKdeStride] population birth proposals
   PriorArgs pa;
   uint64_t seed;
   const double* tw;          // LINAMP fixed (t0, w), [kmax][2]
@@ -171,6 +174,63 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
 // ---------------------------------------------------------------------------
 // Reversible-jump birth/death: one block per particle (Sec. 3.1 nested map).
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Population birth proposal (Sec. 6: the particles of a stage approximate its tempered
+// distribution, so it can serve as the birth proposal).  In z coordinates every
+// parameter's prior is the standard logistic density; the proposal is
+//   q(z) = eps prior_z(z) + (1 - eps)/m sum_i prod_d N(z_d; c_id, h_d^2).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ double log_prior_z(const double* z) {
+  double s = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double a = fabs(z[d]);
+    s += -a - 2.0 * log1p(exp(-a));
+  }
+  return s;
+}
+
+__device__ __forceinline__ double block_max1(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = red[0];
+  for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+// log q(z) for one component z[D]; all threads call it and all get the value
+template <int D>
+__device__ double kde_logq_block(const double* kde, const double* z, double eps, double* red) {
+  const double lp = log_prior_z<D>(z);
+  const int m = (int)kde[0];
+  if (m == 0 || eps >= 1.0) return lp;
+  const double lw = log((1.0 - eps) / (double)m);
+  const double c2 = 0.5 * log(2.0 * kPi);
+  auto term = [&](int i) {   // i = 0: the prior part; i >= 1: centre i - 1
+    if (i == 0) return log(eps) + lp;
+    double e = lw;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const double h = kde[1 + d];
+      const double u = (z[d] - kde[8 + (i - 1) * D + d]) / h;
+      e += -0.5 * u * u - log(h) - c2;
+    }
+    return e;
+  };
+  double mx = -INFINITY;
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) mx = fmax(mx, term(i));
+  mx = block_max1(mx, red);
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) v[0] += exp(term(i) - mx);
+  block_sum<1>(v, red);
+  return mx + log(v[0]);
+}
+
 template <int MODEL, int PREC, int R>
 __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcome, SmemPlan sp) {
   extern __shared__ __align__(16) char smem[];
@@ -209,9 +269,22 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
     }
     if (move == 1) {
       const Rand4 pw = draw(kp.seed, prob, li, stage, round, PU_RJPARAM, 0);
-      for (int d = 0; d < D; ++d) {
-        const double u = u01(pw.w[d]);
-        s_znew[d] = log(u) - log1p(-u);
+      const double* kde = kp.kde + (int64_t)prob * kKdeStride;
+      const Rand4 mw = draw(kp.seed, prob, li, stage, round, PU_RJPARAM, 2);
+      const int m = kp.birth_proposal ? (int)kde[0] : 0;
+      if (m > 0 && u01(mw.w[0]) >= kp.birth_eps) {
+        // from the population mixture: a centre, then a normal step of width h
+        int q = (int)floor(__dmul_rn(u01(mw.w[1]), (double)m));
+        if (q >= m) q = m - 1;
+        for (int d = 0; d < D; ++d)
+          s_znew[d] = __dadd_rn(kde[8 + q * D + d],
+                                __dmul_rn(kde[1 + d], draw_normal(kp.seed, prob, li, stage, round,
+                                                                  PU_RJPARAM, 4 + (uint64_t)d)));
+      } else {
+        for (int d = 0; d < D; ++d) {
+          const double u = u01(pw.w[d]);
+          s_znew[d] = log(u) - log1p(-u);
+        }
       }
     } else if (move == 2) {
       int j = (int)floor(__dmul_rn(u01(w.w[2]), (double)K));
@@ -233,6 +306,16 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   for (int i = tid; i < K * D; i += blockDim.x) zs[i] = zg[i];
   if (move == 1 && tid < D) zs[K * D + tid] = s_znew[tid];
   __syncthreads();
+  // with the population proposal the component's prior no longer cancels:
+  // birth + log prior_z(z_new) - log q(z_new), death + log q(z_j) - log prior_z(z_j)
+  double qcorr = 0.0;
+  if (kp.birth_proposal) {
+    const double* zc = zs + (move == 1 ? K : s_j) * D;
+    const double lq = kde_logq_block<D>(kp.kde + (int64_t)prob * kKdeStride, zc, kp.birth_eps,
+                                        sm.red);
+    const double lp = log_prior_z<D>(zc);
+    qcorr = move == 1 ? lp - lq : lq - lp;
+  }
   const int kp_idx = move == 1 ? K : s_j;      // index of the proposed component
   eval_setup<MODEL, PREC>(pb, kp.pa, move == 1 ? K + 1 : K, zs, sm);
   const int N = (int)pb.n, n1 = (int)pb.n1;   // < 2^24 samples
@@ -304,8 +387,8 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
     const double d_old = v[0] * pb.inv_s2, d_new = v[1] * pb.inv_s2;
     const double beta = kp.beta[prob];
     const double dl = d_old + beta * d_new;
-    const double la = move == 1 ? dl + log(kp.p_death) - log(kp.p_birth)
-                                : dl + log(kp.p_birth) - log(kp.p_death);
+    const double la = (move == 1 ? dl + log(kp.p_death) - log(kp.p_birth)
+                                 : dl + log(kp.p_birth) - log(kp.p_death)) + qcorr;
     int out;
     double* zw = kp.z + gi * (int64_t)sp.kd;
     if (log(s_u) < la) {
@@ -329,6 +412,81 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
     }
     if (outcome) outcome[gi] = out;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Population birth proposal of one problem per block (256 threads): m = kKdeM centres
+// drawn uniformly, with replacement, over all components of the population (draw i:
+// particle slot i of purpose PU_KDE, the stage, round 0), found by a binary search in
+// the inclusive prefix sum of K; bandwidth h_d = sd_d * factor (factor =
+// (4/(D+2))^(1/(D+4)) m^(-1/(D+4)) from the host), at least 1e-3, with the mean and
+// deviation summed in centre order.  kcum: [n_problems][P] int32 scratch.
+// ---------------------------------------------------------------------------
+__global__ void k_kde_build(KParams kp, int32_t* kcum, double* kde_out, double factor,
+                            int stage_arg) {
+  __shared__ int32_t s_part[256];
+  const int prob = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  if (kp.probs[prob].done) return;
+  const int stage = stage_arg >= 0 ? stage_arg : *kp.stage;
+  const int P = kp.P, D = kp.D;
+  const int32_t* K = kp.K + (int64_t)prob * P;
+  int32_t* cum = kcum + (int64_t)prob * P;
+  double* out = kde_out + (int64_t)prob * kKdeStride;
+  const int chunk = (P + T - 1) / T, lo = min(P, tid * chunk), hi = min(P, lo + chunk);
+  int32_t local = 0;
+  for (int i = lo; i < hi; ++i) local += K[i];
+  s_part[tid] = local;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {   // inclusive scan of the per-thread sums
+    const int32_t v = tid >= o ? s_part[tid - o] : 0;
+    __syncthreads();
+    s_part[tid] += v;
+    __syncthreads();
+  }
+  int32_t run = tid > 0 ? s_part[tid - 1] : 0;
+  for (int i = lo; i < hi; ++i) {
+    run += K[i];
+    cum[i] = run;
+  }
+  const int32_t total = s_part[T - 1];
+  __syncthreads();
+  if (total == 0) {
+    if (tid == 0) {
+      out[0] = 0.0;
+      for (int d = 0; d < 4; ++d) out[1 + d] = 1.0;
+    }
+    return;
+  }
+  const int64_t kd = (int64_t)kp.kmax * D;
+  for (int i = tid; i < kKdeM; i += T) {
+    const Rand4 w = draw(kp.seed, prob, (uint64_t)i, stage, 0, PU_KDE, 0);
+    int32_t q = (int32_t)floor(__dmul_rn(u01(w.w[0]), (double)total));
+    if (q >= total) q = total - 1;
+    int a = 0, b = P - 1;   // first particle whose inclusive count exceeds q
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (cum[mid] > q) b = mid; else a = mid + 1;
+    }
+    const int j = q - (cum[a] - K[a]);
+    const double* zp = kp.z + ((int64_t)prob * P + a) * kd + (int64_t)j * D;
+    for (int d = 0; d < D; ++d) out[8 + i * D + d] = zp[d];
+  }
+  __syncthreads();
+  if (tid < D) {
+    const int d = tid;
+    double mean = 0.0;
+    for (int i = 0; i < kKdeM; ++i) mean = __dadd_rn(mean, out[8 + i * D + d]);
+    mean = __ddiv_rn(mean, (double)kKdeM);
+    double var = 0.0;
+    for (int i = 0; i < kKdeM; ++i) {
+      const double e = __dsub_rn(out[8 + i * D + d], mean);
+      var = __dadd_rn(var, __dmul_rn(e, e));
+    }
+    var = __ddiv_rn(var, (double)(kKdeM - 1));
+    const double h = __dmul_rn(__dsqrt_rn(var), factor);
+    out[1 + d] = h < 1e-3 ? 1e-3 : h;
+  }
+  if (tid == 0) out[0] = (double)kKdeM;
 }
 
 // ---------------------------------------------------------------------------
