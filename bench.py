@@ -208,8 +208,8 @@ def _events_ms(stream, fn):
 
 def measure_extras(stream):
     """Secondary measurements: mixed vs FP64 logL+grad throughput, SMC wall time at equal
-    error against the oracle reference, the 64-band batched workload and the paper's
-    segment experiment on its pulse example."""
+    error against the oracle reference, the 64-band batched workload, the paper's segment
+    experiment on its pulse example and the population birth proposal on it."""
     import json as _json
 
     import torch
@@ -316,6 +316,12 @@ def measure_extras(stream):
                                    for x in r["posterior"]],
         "k_mode_all_data": [int(np.argmax(r["prior"][-1]["k_hist"])),
                             int(np.argmax(r["posterior"][-1]["k_hist"]))]}
+    # (5) births from the prior against births from the population mixture (Sec. 6
+    # suggestion): full runs of the same example, and birth acceptance on one mid-run
+    # population under both proposals
+    cmp = experiments.birth_proposal_comparison(wp, mid_stages=40, precision=capi.MIXED,
+                                                stream=stream)
+    out["birth_proposal_paper_pulses"] = cmp
     return out
 
 

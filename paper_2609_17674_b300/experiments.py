@@ -68,3 +68,63 @@ def segment_experiment(wl: Workload, seg_seconds: float = 20.0, precision: int =
         ctx.close()
     return dict(workload=wl.name, segments_s=[nb * pr.dt for nb in bounds], prior=prior,
                 posterior=posterior)
+
+
+def birth_proposal_comparison(wl: Workload, mid_stages: int = 12, rounds: int = 5,
+                              precision: int = capi.MIXED, max_stages: int = 400, stream=None):
+    """Births from the prior against births from the population mixture
+    (tsmc_build_birth_proposal): full prior-start runs with each, and the birth acceptance
+    of both on one population taken after mid_stages stages of the prior-proposal run."""
+    import copy
+
+    import torch
+
+    runs = {}
+    for bp in (0, 1):
+        w = copy.copy(wl)
+        w.birth_proposal = bp
+        ctx = sampler.open_context(w, precision, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = sampler.run_smc(ctx, max_stages=max_stages)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        kh = _k_hist(ctx, w.kmax)
+        runs[bp] = dict(stages=out["n_stages"], wall_s=wall, logz=float(out["logz"][-1][0]),
+                        mean_k=float(np.dot(kh, np.arange(w.kmax + 1))),
+                        reached=bool(out["beta"][-1][0] >= 1.0))
+        ctx.close()
+    # birth acceptance on a common mid-run population
+    w0 = copy.copy(wl)
+    w0.birth_proposal = 0
+    ctx = sampler.open_context(w0, precision, stream=stream)
+    sampler.run_smc(ctx, max_stages=mid_stages)
+    z, K, _, _ = ctx.get_population()
+    z, K = z.clone(), K.clone()
+    beta = ctx.temper_state()[0]
+    ctx.close()
+    acc, outs, m_built = {}, {}, 0
+    for bp in (0, 1):
+        w = copy.copy(wl)
+        w.birth_proposal = bp
+        c = sampler.open_context(w, precision, stream=stream)
+        c.set_population(z.clone(), K.clone(), beta=beta)
+        c.build_birth_proposal(mid_stages)
+        if bp:
+            m_built = c.get_birth_proposal(0)[0]
+        outd = torch.zeros(K.shape[0], dtype=torch.int32, device=z.device)
+        born, proposed, allo = 0, 0, []
+        for r in range(rounds):
+            c.set_population(z.clone(), K.clone(), beta=beta)
+            c.rj_move(mid_stages, r, outd)
+            o = outd.cpu().numpy()
+            allo.append(o.copy())
+            born += int(np.sum(o == 1))
+            proposed += int(np.sum((o == 1) | (o == -1)))
+        acc[bp] = born / max(proposed, 1)
+        outs[bp] = np.concatenate(allo)
+        c.close()
+    return dict(workload=wl.name, prior_births=runs[0], population_births=runs[1],
+                mid_stage=mid_stages, mid_beta=float(beta[0]), proposal_centres=m_built,
+                outcomes_differing=int(np.sum(outs[0] != outs[1])),
+                birth_acceptance_prior=acc[0], birth_acceptance_population=acc[1])
