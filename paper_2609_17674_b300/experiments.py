@@ -101,6 +101,7 @@ def birth_proposal_comparison(wl: Workload, mid_stages: int = 12, rounds: int = 
     sampler.run_smc(ctx, max_stages=mid_stages)
     z, K, _, _ = ctx.get_population()
     z, K = z.clone(), K.clone()
+    torch.cuda.synchronize()   # the clones run on torch's stream, the contexts on theirs
     beta = ctx.temper_state()[0]
     ctx.close()
     acc, outs, m_built = {}, {}, 0
@@ -108,15 +109,20 @@ def birth_proposal_comparison(wl: Workload, mid_stages: int = 12, rounds: int = 
         w = copy.copy(wl)
         w.birth_proposal = bp
         c = sampler.open_context(w, precision, stream=stream)
-        c.set_population(z.clone(), K.clone(), beta=beta)
+        zr, Kr = z.clone(), K.clone()
+        torch.cuda.synchronize()
+        c.set_population(zr, Kr, beta=beta)
         c.build_birth_proposal(mid_stages)
         if bp:
             m_built = c.get_birth_proposal(0)[0]
         outd = torch.zeros(K.shape[0], dtype=torch.int32, device=z.device)
         born, proposed, allo = 0, 0, []
         for r in range(rounds):
-            c.set_population(z.clone(), K.clone(), beta=beta)
+            zr, Kr = z.clone(), K.clone()
+            torch.cuda.synchronize()
+            c.set_population(zr, Kr, beta=beta)
             c.rj_move(mid_stages, r, outd)
+            c.sync()                   # the move runs on the context's stream
             o = outd.cpu().numpy()
             allo.append(o.copy())
             born += int(np.sum(o == 1))
