@@ -35,6 +35,7 @@ class Cfg(C.Structure):
     _fields_ = [
         ("model", C.c_int32), ("D", C.c_int32), ("kmax", C.c_int32), ("kmin", C.c_int32),
         ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
+        ("channels", C.c_int32), ("resp", C.c_double * 4),
         ("n_mut", C.c_int32),
         ("max_depth", C.c_int32), ("schedule", C.c_int32), ("alpha", C.c_double),
         ("p_nuts", C.c_double), ("p_birth", C.c_double), ("p_death", C.c_double),
@@ -107,7 +108,8 @@ class Oracle:
                       if wl.fixed_tw is not None else None)
         self.cfg = Cfg(model=wl.model, D=wl.D, kmax=wl.kmax, kmin=wl.kmin,
                        birth_proposal=wl.birth_proposal,
-                       birth_prior_weight=wl.birth_prior_weight, n_mut=wl.n_mut,
+                       birth_prior_weight=wl.birth_prior_weight, channels=wl.channels,
+                       resp=(C.c_double * 4)(*wl.resp), n_mut=wl.n_mut,
                        max_depth=wl.max_depth, schedule=wl.schedule, alpha=wl.alpha,
                        p_nuts=wl.p_nuts, p_birth=wl.p_birth, p_death=wl.p_death,
                        lo=(C.c_double * 4)(*lo), hi=(C.c_double * 4)(*hi), logmask=wl.logmask,

@@ -158,6 +158,18 @@ double orc_template(const orc_cfg* c, int k, const double* th, double t, double*
   return A * cph;
 }
 
+/* Two data channels (Sec. 5.2: the noise-orthogonal channels A and E): with a */
+/* simplified response, channel ch sees r_ch A cos(phi(t) + delta_ch).        */
+double orc_template_ch(const orc_cfg* c, int k, const double* th, double t, int ch,
+                       double* dh) {
+  if (c->channels != 2) return orc_template(c, k, th, t, dh);
+  const double r = c->resp[2 * ch], dl = c->resp[2 * ch + 1];
+  double thc[4] = {r * th[0], th[1], th[2], th[3] + dl};
+  const double h = orc_template(c, k, thc, t, dh);
+  if (dh) dh[0] = r * dh[0];
+  return h;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Likelihood (white Gaussian noise, time domain):                            */
 /*   r_n = d_n - sum_{k<K} h(t_n; theta_k)                                     */
@@ -187,15 +199,18 @@ void orc_logl_grad(const orc_cfg* c, const orc_data* dat, const double* z, int32
   double aacc[ORC_MAXKD], facc[ORC_MAXKD];
   for (int i = 0; i < KD; ++i) { gacc[i].s = gacc[i].c = 0; aacc[i] = 0; facc[i] = 0; }
   double dh[4];
+  /* two channels: samples [0, n/2) are channel A, [n/2, n) channel E, same times */
+  const int64_t nc = c->channels == 2 ? dat->n / 2 : dat->n;
   for (int64_t n = 0; n < dat->n; ++n) {
-    double t = dat->t_origin + (double)n * dat->dt;
+    const int ch = (int)(n / nc);
+    double t = dat->t_origin + (double)(n - ch * nc) * dat->dt;
     double hs = 0.0;
-    for (int k = 0; k < K; ++k) hs += orc_template(c, k, &theta[k * D], t, NULL);
+    for (int k = 0; k < K; ++k) hs += orc_template_ch(c, k, &theta[k * D], t, ch, NULL);
     double r = dat->d[n] - hs;
     double cn = (n < dat->n1) ? 1.0 : beta;
     if (n < dat->n1) nadd(&s_old, r * r); else nadd(&s_new, r * r);
     for (int k = 0; k < K; ++k) {
-      orc_template(c, k, &theta[k * D], t, dh);
+      orc_template_ch(c, k, &theta[k * D], t, ch, dh);
       for (int d = 0; d < D; ++d) {
         double term = cn * r * dh[d];
         nadd(&gacc[k * D + d], term);
@@ -331,12 +346,14 @@ void orc_rj_move_q(const orc_cfg* c, const orc_data* dat, int32_t problem, int32
       for (int d = 0; d < D; ++d) th_new[d] = th_all[j * D + d];
     }
     nsum a_old = {0, 0}, a_new = {0, 0};
+    const int64_t nc = c->channels == 2 ? dat->n / 2 : dat->n;
     for (int64_t n = 0; n < dat->n; ++n) {
-      double t = dat->t_origin + (double)n * dat->dt;
+      const int ch = (int)(n / nc);
+      double t = dat->t_origin + (double)(n - ch * nc) * dat->dt;
       double hs = 0.0;
-      for (int q = 0; q < k; ++q) hs += orc_template(c, q, &th_all[q * D], t, NULL);
+      for (int q = 0; q < k; ++q) hs += orc_template_ch(c, q, &th_all[q * D], t, ch, NULL);
       double r = dat->d[n] - hs;
-      double h = orc_template(c, birth ? k : j, th_new, t, NULL);
+      double h = orc_template_ch(c, birth ? k : j, th_new, t, ch, NULL);
       double term = birth ? (r * h - 0.5 * h * h) : -(r * h + 0.5 * h * h);
       if (n < dat->n1) nadd(&a_old, term); else nadd(&a_new, term);
     }

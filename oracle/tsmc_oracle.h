@@ -41,6 +41,9 @@ typedef struct {
   int32_t kmin;           /* minimum component count of the K prior (0 <= kmin <= kmax) */
   int32_t birth_proposal; /* 0: births from the prior; 1: population mixture (orc_kde) */
   double birth_prior_weight;      /* epsilon: prior weight of the population mixture */
+  int32_t channels;       /* sinusoid: 1, or 2 data channels (A, E) */
+  double resp[4];         /* two channels: (r_A, delta_A, r_E, delta_E), channel c sees
+                             r_c A cos(phi(t) + delta_c) */
   int32_t n_mut;          /* mutation rounds per stage */
   int32_t max_depth;      /* NUTS maximum tree depth */
   int32_t schedule;       /* ORC_SCHED_ROUNDS or ORC_SCHED_MIXTURE */
@@ -79,6 +82,9 @@ void orc_z_to_theta(const orc_cfg* c, int d, double z, double* theta, double* dt
 
 /* single template and its parameter derivatives at time t (component k for LINAMP) */
 double orc_template(const orc_cfg* c, int k, const double* theta, double t, double* dh);
+/* the same in data channel ch (two-channel sinusoids: response r_ch, delta_ch) */
+double orc_template_ch(const orc_cfg* c, int k, const double* theta, double t, int ch,
+                       double* dh);
 
 /* logL parts, tempered log target and its gradient for one particle */
 void orc_logl_grad(const orc_cfg* c, const orc_data* dat, const double* z, int32_t K, double beta,

@@ -71,6 +71,8 @@ class Workload:
     kmin: int = 0             # K prior U{kmin..kmax}
     birth_proposal: int = 0   # 0: births from the prior; 1: population mixture
     birth_prior_weight: float = 0.2   # prior weight of the population mixture
+    channels: int = 1         # sinusoids: 2 = channels A and E, data [A samples, E samples]
+    resp: tuple = (1.0, 0.0, 1.0, 0.0)   # (r_A, delta_A, r_E, delta_E)
 
     @property
     def D(self) -> int:
@@ -137,6 +139,44 @@ def sinusoid_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F
     truth = np.stack([A, f, fd, p0], axis=1)
     return Problem(d=d, t_origin=0.0, dt=dt, sigma=sigma, truth=truth,
                    lo=(a_lo, f_lo, 0.0, 0.0), hi=(a_hi, f_hi, GB_FDOT_HI, 2.0 * math.pi))
+
+
+# Two noise-orthogonal channels A and E (Sec. 5.2), flat PSD, noise-free: channel c sees
+# r_c A cos(phi(t) + delta_c).  The simplified synthetic response used here (the real one
+# needs the LISA response, not available) gives E 0.8 of A's sensitivity in quadrature.
+AE_RESP = (1.0, 0.0, 0.8, 0.5 * math.pi)
+
+
+def ae_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F_HI,
+               resp=AE_RESP) -> Problem:
+    """Two-channel sinusoids, noise-free, rho^2 = sum_c (h_c | h_c) ~ U[10, 40]^2 per source
+    (flat PSD: the frequency-domain inner product equals sum_n a_n b_n / sigma^2 with
+    sigma^2 = S / (2 dt)); data [channel A samples, channel E samples]."""
+    t = np.arange(n, dtype=np.float64) * dt
+    f = f_lo + (f_hi - f_lo) * rng.random(k_true)
+    fd = GB_FDOT_HI * rng.random(k_true)
+    p0 = 2.0 * math.pi * rng.random(k_true)
+    rho = 10.0 + 30.0 * rng.random(k_true)
+    d = np.zeros(2 * n)
+    A = np.empty(k_true)
+    for k in range(k_true):
+        ca = resp[0] * np.cos(_sin_phase(t, f[k], fd[k], p0[k] + resp[1]))
+        ce = resp[2] * np.cos(_sin_phase(t, f[k], fd[k], p0[k] + resp[3]))
+        A[k] = rho[k] * sigma / math.sqrt(float(np.sum(ca * ca) + np.sum(ce * ce)))
+        d[:n] += A[k] * ca
+        d[n:] += A[k] * ce
+    a_lo, a_hi = gb_amp_bounds(n, dt, sigma, 0.5 * (f_lo + f_hi))
+    truth = np.stack([A, f, fd, p0], axis=1)
+    return Problem(d=d, t_origin=0.0, dt=dt, sigma=sigma, truth=truth,
+                   lo=(a_lo, f_lo, 0.0, 0.0), hi=(a_hi, f_hi, GB_FDOT_HI, 2.0 * math.pi))
+
+
+def ae_workload(name, n, k_true, kmax, P, seed, resp=AE_RESP, **kw) -> Workload:
+    """Galactic-binary band in channels A and E (n samples per channel)."""
+    rng = _rng(seed)
+    pr = ae_problem(rng, n, k_true, resp=resp)
+    return Workload(name=name, model=SINUSOID, kmax=kmax, P=P, problems=[pr], lo=pr.lo,
+                    hi=pr.hi, logmask=0b0001, seed=seed, channels=2, resp=tuple(resp), **kw)
 
 
 def pulse_workload(name, n, k_true, kmax, P, seed, sigma=0.1, n_problems=1, **kw) -> Workload:
