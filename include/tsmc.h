@@ -79,6 +79,15 @@ typedef struct {
                              1: from the population mixture described at
                              tsmc_build_birth_proposal (Sec. 6 suggestion).  LINAMP: ignored */
   double birth_prior_weight;  /* eps in (0, 1] of that mixture (used when birth_proposal = 1) */
+  int32_t channels;       /* 0 or 1: one data channel.  2 (TSMC_SINUSOID only): the two
+                             noise-orthogonal channels A and E of Sec. 5.2; each problem's
+                             data are channel A's samples then channel E's (same times,
+                             2 x a multiple of 32 samples), channel c sees
+                             response[2c] A cos(phi(t) + response[2c+1]).  With a flat PSD S
+                             the frequency-domain likelihood of eq. gw_likelihood equals this
+                             time-domain one with sigma^2 = S / (2 dt) (Parseval; DC and
+                             Nyquist bins aside).  No tsmc_assimilate for two channels. */
+  double response[4];     /* channels = 2: (r_A, delta_A, r_E, delta_E), r_c > 0 */
 } tsmc_config;
 
 /* Workspace size for a configuration and per-problem sample capacities

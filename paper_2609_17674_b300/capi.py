@@ -67,6 +67,7 @@ class Config(C.Structure):
         ("threads", C.c_int32), ("samples_per_thread", C.c_int32),
         ("pulse_window", C.c_int32), ("kmin", C.c_int32),
         ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
+        ("channels", C.c_int32), ("response", C.c_double * 4),
     ]
 
 

@@ -110,6 +110,13 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->birth_proposal != 0 && cfg->birth_proposal != 1) return TSMC_EINVAL;
   if (cfg->birth_proposal == 1 && !(cfg->birth_prior_weight > 0.0 && cfg->birth_prior_weight <= 1.0))
     return TSMC_EINVAL;
+  if (cfg->channels < 0 || cfg->channels > 2) return TSMC_EINVAL;
+  if (cfg->channels == 2) {
+    if (cfg->model != TSMC_SINUSOID) return TSMC_EINVAL;
+    for (int q = 0; q < 4; ++q)
+      if (!std::isfinite(cfg->response[q])) return TSMC_EINVAL;
+    if (!(cfg->response[0] > 0.0) || !(cfg->response[2] > 0.0)) return TSMC_EINVAL;
+  }
   return TSMC_OK;
 }
 
@@ -200,6 +207,7 @@ SmemPlan smem_plan(Ctx* c, bool fisher, int depth) {
   sp.fisher = fisher;
   const int span = 32 * c->R;
   sp.nwr = c->cfg.precision == TSMC_MIXED ? (int)((c->nmax + span - 1) / span) : 0;
+  sp.nch = c->cfg.channels == 2 ? 2 : 1;
   return sp;
 }
 
@@ -626,6 +634,14 @@ tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, i
   }
   pd.f_to = split_df(t_origin);
   pd.f_dt = split_df(dt);
+  pd.nch = c->cfg.channels == 2 ? 2 : 1;
+  pd.nc = n / pd.nch;
+  if (pd.nch == 2 && (n % 2 != 0 || pd.nc % 32 != 0))
+    return fail(c, TSMC_EINVAL, "two-channel data need 2 x (a multiple of 32) samples");
+  for (int q = 0; q < 4; ++q) {
+    pd.resp[q] = pd.nch == 2 ? c->cfg.response[q] : (q % 2 == 0 ? 1.0 : 0.0);
+    pd.f_resp[q] = (float)pd.resp[q];
+  }
   TRY_CUDA(c, cudaMemcpyAsync(const_cast<double*>(pd.d64), d_host, sizeof(double) * n,
                               cudaMemcpyHostToDevice, c->stream));
   pre(c, KC_OTHER);
@@ -879,6 +895,7 @@ tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new, int
   if (!c->pop_ready || !c->has_data[problem]) return fail(c, TSMC_ESTATE, "no population");
   ProbDev& pd = c->probs_host[problem];
   if (!d_new || n_new <= 0 || pd.n + n_new > pd.cap) return fail(c, TSMC_EINVAL, "bad sample count");
+  if (pd.nch == 2) return fail(c, TSMC_EINVAL, "two-channel problems take no appended samples");
   if (!all_finite(d_new, n_new)) return fail(c, TSMC_ENONFINITE, "non-finite data");
   TRY_CUDA(c, cudaMemcpyAsync(const_cast<double*>(pd.d64) + pd.n, d_new, sizeof(double) * n_new,
                               cudaMemcpyHostToDevice, c->stream));

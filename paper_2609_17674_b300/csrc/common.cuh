@@ -85,6 +85,13 @@ struct ProbDev {
   // double-float (hi, lo) copies for FP32 arithmetic on the mixed path:
   // t_origin, dt, and per parameter the map's offset and span (log-space if log-uniform)
   float2 f_to, f_dt, f_off[4], f_span[4];
+  // sinusoids in two data channels (A, E): samples [0, nc) are channel A, [nc, 2 nc) channel
+  // E at the same times; channel c sees resp[2c] A cos(phi(t) + resp[2c+1]).  nch = 1: one
+  // channel, nc = n.
+  int64_t nc;
+  int32_t nch, pad_;
+  double resp[4];
+  float f_resp[4];
 };
 
 // ---------------------------------------------------------------------------

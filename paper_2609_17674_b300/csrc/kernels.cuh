@@ -38,9 +38,10 @@ struct SmemPlan {
   int depth;       // NUTS checkpoint levels (0 for non-NUTS kernels)
   bool fisher;
   int nwr;         // warp ranges of the longest problem (active-component masks)
+  int nch;         // data channels (mixed-path constants per channel)
   __host__ __device__ size_t eval_bytes() const {
     return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4 + 64) +
-           sizeof(float) * (size_t)kd * NCF + sizeof(uint32_t) * 2 * (size_t)nwr + 32;
+           sizeof(float) * (size_t)kd * NCF * nch + sizeof(uint32_t) * 2 * (size_t)nwr + 32;
   }
   __host__ __device__ size_t nuts_bytes() const {
     return sizeof(double) * (size_t)kd * (14 + 2 * (size_t)(depth + 1));   // 8-byte slots
@@ -69,7 +70,8 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
   sm.exptab = reinterpret_cast<float2*>(d); d += 64;
   if (reinterpret_cast<uintptr_t>(d) & 8) d += 1;   // float4 loads of the constants
   sm.cf = reinterpret_cast<float*>(d);
-  sm.wmask = reinterpret_cast<uint32_t*>(sm.cf + (size_t)sp.kd * NCF);
+  sm.cfch = sp.kd * NCF;
+  sm.wmask = reinterpret_cast<uint32_t*>(sm.cf + (size_t)sp.kd * NCF * sp.nch);
   p = reinterpret_cast<char*>(sm.wmask + 2 * (size_t)sp.nwr);
   // keep 8-byte alignment for what follows
   p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
@@ -327,18 +329,22 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
     if (wfirst >= N) continue;
     const float wf = (float)wfirst, wl = (float)(wfirst + 32 * R - 1);
     const int m = base + tid * R;
+    // two-channel sinusoids: the thread's channel and local sample index
+    const int ch = (MODEL == SINUSOID && pb.nch == 2 && m >= (int)pb.nc) ? 1 : 0;
+    const int ml = m - ch * (int)pb.nc;
     if (PREC == MIXED) {
+      const float* cfb = sm.cf + ch * sm.cfch;
       const bool win = MODEL != SINUSOID && kp.pa.window;
       float cfp[NCF];
-      load_cf(sm.cf + kp_idx * NCF, cfp);
+      load_cf(cfb + kp_idx * NCF, cfp);
       if (win && outside_support(cfp, wf, wl)) continue;   // proposal is zero here
       float r[R], hp[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) r[j] = (m + j < N) ? pb.d32[m + j] : 0.0f;
-      const float mf = (float)m;
+      const float mf = (float)ml;
       for (int k = 0; k < K; ++k) {
         float cf[NCF], h[R];
-        load_cf(sm.cf + k * NCF, cf);
+        load_cf(cfb + k * NCF, cf);
         if (win && outside_support(cf, wf, wl)) continue;
         mixed_vals<MODEL, R>(cf, mf, h);
 #pragma unroll
@@ -360,21 +366,22 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
       double hs[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) hs[j] = 0.0;
+      double thb[4], thpb[4];
       for (int k = 0; k < K; ++k) {
-        const double* th = sm.th + k * D;
+        const double* th = chan_theta<MODEL>(pb, ch, sm.th + k * D, thb);
         const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
         const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
 #pragma unroll
         for (int j = 0; j < R; ++j)
-          hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), nullptr));
+          hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, ml + j), nullptr));
       }
-      const double* thp = sm.th + kp_idx * D;
+      const double* thp = chan_theta<MODEL>(pb, ch, sm.th + kp_idx * D, thpb);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int n = m + j;
         if (n >= N) continue;
         const double r = __dadd_rn(pb.d64[n], -hs[j]);
-        const double h = fp64_val<MODEL>(thp, 0.0, 0.0, time_of(pb, n), nullptr);
+        const double h = fp64_val<MODEL>(thp, 0.0, 0.0, time_of(pb, ml + j), nullptr);
         const double rh = __dmul_rn(r, h), hh = __dmul_rn(__dmul_rn(0.5, h), h);
         const double t = move == 1 ? __dadd_rn(rh, -hh) : -__dadd_rn(rh, hh);
         if (n < n1) a_old += t; else a_new += t;

@@ -498,7 +498,8 @@ struct EvalSmem {
   double* dth;    // [KDmax] dtheta/dz
   double* pg;     // [KDmax] prior gradient
   double* pc;     // [KDmax] prior curvature
-  float* cf;      // [kmax][NCF] mixed-path constants
+  float* cf;      // [channels][kmax][NCF] mixed-path constants
+  int cfch;       // floats between the constant sets of two channels
   double* wacc;   // [nwarps][KDmax] per-warp gradient slot sums
   double* wfis;   // [nwarps][KDmax] per-warp Gauss-Newton slot sums
   double* red;    // [32*4] reduction scratch
@@ -921,6 +922,19 @@ __device__ __forceinline__ void load_cf(const float* cf, float (&o)[NCF]) {
 // Mixed path: per-lane slot sums and per-thread energies are FP32 with Kahan
 // compensation across segments; the cross-warp totals are FP64.
 // ---------------------------------------------------------------------------
+// FP64 parameters of a component as seen in data channel ch (two-channel sinusoids:
+// amplitude r_ch A, phase offset delta_ch); other models and one channel: th itself
+template <int MODEL>
+__device__ __forceinline__ const double* chan_theta(const ProbDev& pb, int ch, const double* th,
+                                                    double* buf) {
+  if (MODEL != SINUSOID || pb.nch != 2) return th;
+  buf[0] = __dmul_rn(pb.resp[2 * ch], th[0]);
+  buf[1] = th[1];
+  buf[2] = th[2];
+  buf[3] = __dadd_rn(th[3], pb.resp[2 * ch + 1]);
+  return buf;
+}
+
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER>
 __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
                                 const double* z, EvalSmem& sm, double* grad_out,
@@ -945,17 +959,21 @@ __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, d
     if (wfirst >= N) continue;  // whole warp past the end (warp-uniform)
     const int64_t m = base + (int64_t)tid * R;
     const double mine = (double)(m < N ? (m + R <= N ? R : N - m) : 0);
+    // two-channel sinusoids: the thread's channel and local sample index
+    const int ch = (MODEL == SINUSOID && pb.nch == 2 && m >= pb.nc) ? 1 : 0;
+    const int64_t ml = m - ch * pb.nc;
+    double thb[4];
     double hs[R], r[R];
     done += mine * K;
 #pragma unroll
     for (int j = 0; j < R; ++j) hs[j] = 0.0;
     for (int k = 0; k < K; ++k) {
-      const double* th = sm.th + k * D;
+      const double* th = chan_theta<MODEL>(pb, ch, sm.th + k * D, thb);
       const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
       const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
 #pragma unroll
       for (int j = 0; j < R; ++j)
-        hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), nullptr));
+        hs[j] = __dadd_rn(hs[j], fp64_val<MODEL>(th, tw0, tw1, time_of(pb, ml + j), nullptr));
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -968,14 +986,15 @@ __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, d
     }
     if (GRAD || FISHER) {
       for (int k = 0; k < K; ++k) {
-        const double* th = sm.th + k * D;
+        const double* th = chan_theta<MODEL>(pb, ch, sm.th + k * D, thb);
         const double tw0 = MODEL == PULSE_LINAMP ? sm.tw[2 * k] : 0.0;
         const double tw1 = MODEL == PULSE_LINAMP ? sm.tw[2 * k + 1] : 0.0;
         double o[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           double dh[4];
-          fp64_val<MODEL>(th, tw0, tw1, time_of(pb, m + j), dh);
+          fp64_val<MODEL>(th, tw0, tw1, time_of(pb, ml + j), dh);
+          if (MODEL == SINUSOID && pb.nch == 2) dh[0] = __dmul_rn(pb.resp[2 * ch], dh[0]);
           const int64_t n = m + j;
           const double cn = n < N ? (n < n1 ? 1.0 : beta) : 0.0;
 #pragma unroll
@@ -1104,7 +1123,13 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     float* cf = sm.cf + k * NCF;
     if (MODEL == SINUSOID) {
-      sin_prep32(th[k * D], sm.wacc[k], th[k * D + 2], th[k * D + 3], pb, cf);
+      if (pb.nch == 2) {   // channel c: amplitude r_c A, phase offset delta_c
+        for (int ch = 0; ch < 2; ++ch)
+          sin_prep32(pb.f_resp[2 * ch] * th[k * D], sm.wacc[k], th[k * D + 2],
+                     th[k * D + 3] + pb.f_resp[2 * ch + 1], pb, cf + ch * sm.cfch);
+      } else {
+        sin_prep32(th[k * D], sm.wacc[k], th[k * D + 2], th[k * D + 3], pb, cf);
+      }
     } else if (MODEL == PULSE) {
       const float A = th[k * D], w = th[k * D + 2];
       pulse_prep_df(A, DF{th[k * D + 1], th_lo[k * D + 1]}, w, pb, cf);
@@ -1171,7 +1196,12 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
 #pragma unroll
       for (int j = 0; j < R; ++j) slot<MODEL, R>(r, j) = (m + j < N) ? pb.d32[m + j] : 0.0f;
     }
-    const float mf = (float)m;
+    // two-channel sinusoids: the thread's channel (its R samples never straddle), its
+    // local sample index and that channel's constants; r_c scales the adjoint sums
+    const int ch = (MODEL == SINUSOID && pb.nch == 2 && m >= (int)pb.nc) ? 1 : 0;
+    const float mf = (float)(m - ch * (int)pb.nc);
+    const float* cfb = sm.cf + ch * sm.cfch;
+    const float rch = pb.f_resp[2 * ch];
     // components active on this warp's range, ascending (all K without the window)
     uint32_t act[2];
     if (win) {
@@ -1195,14 +1225,14 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
           const int kb = __ffsll((long long)bits) - 1;
           bits &= bits - 1ull;
           float cf[2][NCF];
-          load_cf(sm.cf + ka * NCF, cf[0]);
-          load_cf(sm.cf + kb * NCF, cf[1]);
+          load_cf(cfb + ka * NCF, cf[0]);
+          load_cf(cfb + kb * NCF, cf[1]);
           mixed_sub<MODEL, R, 2>(cf, mf, r);
           continue;
         }
       }
       float cf[1][NCF];
-      load_cf(sm.cf + ka * NCF, cf[0]);
+      load_cf(cfb + ka * NCF, cf[0]);
       mixed_sub<MODEL, R, 1>(cf, mf, r);
     }
     // residual energy and the adjoint weights rc = c_n r_n / sigma^2
@@ -1229,17 +1259,23 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
             const int kb = __ffsll((long long)bits) - 1;
             bits &= bits - 1ull;
             float cf[2][NCF], o[2][4];
-            load_cf(sm.cf + ka * NCF, cf[0]);
-            load_cf(sm.cf + kb * NCF, cf[1]);
+            load_cf(cfb + ka * NCF, cf[0]);
+            load_cf(cfb + kb * NCF, cf[1]);
             mixed_adj<MODEL, R, 2>(cf, mf, r, o);
+            if (MODEL == SINUSOID && pb.nch == 2)
+#pragma unroll
+              for (int d = 0; d < 4; ++d) { o[0][d] *= rch; o[1][d] *= rch; }
             warp_accumulate<D>(o[0], lane, ka, gacc);
             warp_accumulate<D>(o[1], lane, kb, gacc);
             continue;
           }
         }
         float cf[1][NCF], o[1][4];
-        load_cf(sm.cf + ka * NCF, cf[0]);
+        load_cf(cfb + ka * NCF, cf[0]);
         mixed_adj<MODEL, R, 1>(cf, mf, r, o);
+        if (MODEL == SINUSOID && pb.nch == 2)
+#pragma unroll
+          for (int d = 0; d < 4; ++d) o[0][d] *= rch;
         warp_accumulate<D>(o[0], lane, ka, gacc);
       }
     }
@@ -1255,8 +1291,11 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
       for (uint32_t bits = act[half]; bits; bits &= bits - 1u) {
         const int k = (half << 5) + __ffs(bits) - 1;
         float cf[NCF], o[4];
-        load_cf(sm.cf + k * NCF, cf);
+        load_cf(cfb + k * NCF, cf);
         mixed_fis<MODEL, R>(cf, mf, cw, (float)pb.t_origin, (float)pb.dt, o);
+        if (MODEL == SINUSOID && pb.nch == 2)
+#pragma unroll
+          for (int d = 0; d < 4; ++d) o[d] *= rch * rch;
         warp_accumulate<D>(o, lane, k, facc);
       }
     }

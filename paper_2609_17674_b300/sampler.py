@@ -18,7 +18,8 @@ def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
     return capi.Config(model=wl.model, precision=precision, schedule=wl.schedule,
                        n_problems=len(wl.problems), particles=wl.P, kmax=wl.kmax, kmin=wl.kmin,
                        birth_proposal=wl.birth_proposal,
-                       birth_prior_weight=wl.birth_prior_weight,
+                       birth_prior_weight=wl.birth_prior_weight, channels=wl.channels,
+                       response=(capi.C.c_double * 4)(*wl.resp),
                        n_mut=wl.n_mut, max_depth=wl.max_depth, alpha=wl.alpha, p_nuts=wl.p_nuts,
                        p_birth=wl.p_birth, p_death=wl.p_death, amp_mean=wl.amp_mean,
                        amp_sd=wl.amp_sd, seed=wl.seed, threads=threads,
