@@ -609,6 +609,8 @@ tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, i
   if (!(sigma > 0.0) || !std::isfinite(dt) || !std::isfinite(t_origin) || !std::isfinite(sigma))
     return fail(c, TSMC_EINVAL, "bad grid or noise level");
   if (!all_finite(d_host, n)) return fail(c, TSMC_ENONFINITE, "non-finite data");
+  if (c->cfg.channels == 2 && (n % 64 != 0))
+    return fail(c, TSMC_EINVAL, "two-channel data need 2 x (a multiple of 32) samples");
   ProbDev& pd = c->probs_host[problem];
   pd.n = n;
   pd.n1 = 0;
@@ -636,8 +638,6 @@ tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, i
   pd.f_dt = split_df(dt);
   pd.nch = c->cfg.channels == 2 ? 2 : 1;
   pd.nc = n / pd.nch;
-  if (pd.nch == 2 && (n % 2 != 0 || pd.nc % 32 != 0))
-    return fail(c, TSMC_EINVAL, "two-channel data need 2 x (a multiple of 32) samples");
   for (int q = 0; q < 4; ++q) {
     pd.resp[q] = pd.nch == 2 ? c->cfg.response[q] : (q % 2 == 0 ? 1.0 : 0.0);
     pd.f_resp[q] = (float)pd.resp[q];
