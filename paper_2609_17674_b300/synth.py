@@ -148,7 +148,7 @@ AE_RESP = (1.0, 0.0, 0.8, 0.5 * math.pi)
 
 
 def ae_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F_HI,
-               resp=AE_RESP) -> Problem:
+               resp=AE_RESP, noise=False) -> Problem:
     """Two-channel sinusoids, noise-free, rho^2 = sum_c (h_c | h_c) ~ U[10, 40]^2 per source
     (flat PSD: the frequency-domain inner product equals sum_n a_n b_n / sigma^2 with
     sigma^2 = S / (2 dt)); data [channel A samples, channel E samples]."""
@@ -165,16 +165,18 @@ def ae_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F_HI,
         A[k] = rho[k] * sigma / math.sqrt(float(np.sum(ca * ca) + np.sum(ce * ce)))
         d[:n] += A[k] * ca
         d[n:] += A[k] * ce
+    if noise:   # white noise of the flat PSD (the paper's example is noise-free)
+        d = d + sigma * rng.standard_normal(2 * n)
     a_lo, a_hi = gb_amp_bounds(n, dt, sigma, 0.5 * (f_lo + f_hi))
     truth = np.stack([A, f, fd, p0], axis=1)
     return Problem(d=d, t_origin=0.0, dt=dt, sigma=sigma, truth=truth,
                    lo=(a_lo, f_lo, 0.0, 0.0), hi=(a_hi, f_hi, GB_FDOT_HI, 2.0 * math.pi))
 
 
-def ae_workload(name, n, k_true, kmax, P, seed, resp=AE_RESP, **kw) -> Workload:
+def ae_workload(name, n, k_true, kmax, P, seed, resp=AE_RESP, noise=False, **kw) -> Workload:
     """Galactic-binary band in channels A and E (n samples per channel)."""
     rng = _rng(seed)
-    pr = ae_problem(rng, n, k_true, resp=resp)
+    pr = ae_problem(rng, n, k_true, resp=resp, noise=noise)
     return Workload(name=name, model=SINUSOID, kmax=kmax, P=P, problems=[pr], lo=pr.lo,
                     hi=pr.hi, logmask=0b0001, seed=seed, channels=2, resp=tuple(resp), **kw)
 

@@ -2,7 +2,9 @@
 a flat PSD, computed in the time domain; the oracle's pins tie it to the frequency-domain
 inner product) through the C ABI against the oracle: evaluation, Gauss-Newton sums,
 reversible jump, NUTS and one SMC stage, a full-size band on a sample of particles, and the
-argument checks."""
+argument checks.  The mixed-path comparisons use data with white noise: on noise-free data
+a particle at the injection has a residual near zero, against which FP32 template rounding
+(relative to the signal) is not a meaningful relative error."""
 import numpy as np
 import pytest
 
@@ -12,12 +14,6 @@ from gpu_helpers import (TOL, assert_eval_parity, context_with_population, dev_t
                          population, torch)
 
 pytestmark = pytest.mark.gpu
-
-
-def _energy(wl):
-    """1/2 sum d^2 / sigma^2: the conditioning scale of ll for noise-free data."""
-    pr = wl.problems[0]
-    return 0.5 * float(np.sum(pr.d ** 2)) / pr.sigma ** 2
 
 
 def _near_injection(wl, z, K, every=2, jitter=0.01):
@@ -34,20 +30,20 @@ def _near_injection(wl, z, K, every=2, jitter=0.01):
 @pytest.mark.parametrize("n", [4096, 1056])
 def test_eval_parity(prec, n):
     t = torch()
-    wl = synth.ae_workload("t", n, 3, 5, 24, 41)
+    wl = synth.ae_workload("t", n, 3, 5, 24, 41, noise=True)
     z, K = _near_injection(wl, *population(wl, 5, 24))
     ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.37)
     lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.37], t.float64), grad=True)
     t.cuda.synchronize()
     ora = oracle.Oracle(wl)
     res = ora.logl_grad(z, K, 0.37)
-    assert_eval_parity(ora, res, lo, ln, lp, g, K, TOL[prec], 4, lscale=_energy(wl))
+    assert_eval_parity(ora, res, lo, ln, lp, g, K, TOL[prec], 4)
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
 def test_fisher_parity(prec):
     t = torch()
-    wl = synth.ae_workload("t", 4096, 3, 4, 12, 42)
+    wl = synth.ae_workload("t", 4096, 3, 4, 12, 42, noise=True)
     z, K = _near_injection(wl, *population(wl, 9, 12))
     ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.5)
     _, _, _, _, fis = ctx.eval(zd, Kd, dev_tensor([0.5], t.float64), grad=True, fisher=True)
@@ -122,15 +118,14 @@ def test_smc_stage_matches_oracle_fp64():
 def test_full_size_band_sampled():
     """2^18 samples per channel (2^19 in all), K_max = 30, P = 1024; oracle on a sample."""
     t = torch()
-    wl = synth.ae_workload("gb_ae", 1 << 18, 10, 30, 1024, 46)
+    wl = synth.ae_workload("gb_ae", 1 << 18, 10, 30, 1024, 46, noise=True)
     z, K = _near_injection(wl, *population(wl, 1, 1024), every=7, jitter=1e-4)
     ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.9)
     lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.9], t.float64), grad=True)
     t.cuda.synchronize()
     idx = np.array([0, 1, 2, 3, 9, 16])
     res = oracle.Oracle(wl).logl_grad(z[idx], K[idx], 0.9)
-    assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[capi.MIXED], 4,
-                       lscale=_energy(wl))
+    assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[capi.MIXED], 4)
 
 
 def test_two_channel_arguments_checked():
