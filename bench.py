@@ -269,6 +269,26 @@ def measure_extras(stream):
         res["oracle_logz"] = float(gz.mean())
         res["fp64_over_mixed_wall"] = res["fp64"]["wall_s_per_run"] / res["mixed"]["wall_s_per_run"]
         out["smc_equal_error_pulse_n1024_p512"] = res
+    # (2b) two channels A and E (eq. gw_likelihood, flat PSD, simplified response):
+    # 2^18 samples per channel, K_max = 30, P = 4096, logL + gradient and one NUTS round;
+    # the value counts K_p x 2^19 component*samples (both channels)
+    wa = synth.ae_workload("gb_ae_n262144x2_k10_p4096", 1 << 18, 10, 30, 4096, 1007)
+    za, Ka = synth.prior_population(wa, 3)
+    zda, Kda = torch.as_tensor(za, device="cuda"), torch.as_tensor(Ka, device="cuda")
+    ctx = sampler.open_context(wa, capi.MIXED, stream=stream)
+    ctx.set_population(zda, Kda, beta=[1e-3])
+    ba = torch.tensor([0.5], dtype=torch.float64, device="cuda")
+    ga = torch.empty_like(zda)
+    csa = float(Ka.sum()) * wa.problems[0].n
+    msa = min(_events_ms(stream, lambda: ctx.eval(zda, Kda, ba, grad=True, g=ga)) for _ in range(3))
+    ctx.update_metric()
+    ctx.counters(reset=True)
+    msn = _events_ms(stream, lambda: ctx.nuts_move(0, 0))
+    (_, cna, _, _), _ = ctx.counters(reset=True)
+    out["two_channel_band"] = {"workload": wa.name, "unit": UNIT,
+                               "logl_grad_kernel": csa / (msa * 1e-3),
+                               "nuts_transition": cna / (msn * 1e-3), "nuts_ms": msn}
+    ctx.close()
     # (3) 64 independent GB bands (N_b 2^14..2^18, P=2048 each) in one launch
     w5 = synth.config5()
     nb = len(w5.problems)
