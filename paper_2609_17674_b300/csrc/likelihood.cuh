@@ -1237,15 +1237,29 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     }
     // residual energy and the adjoint weights rc = c_n r_n / sigma^2
     float so = 0.f, sn = 0.f;
+    if (m >= n1 && m + R <= N) {
+      // every sample of the thread valid and new: packed products, two packed partial sums
+      const float2 w = f2(beta_f * inv_s2_f);
+      float2 acc0 = f2(0.f), acc1 = f2(0.f);
 #pragma unroll
-    for (int j = 0; j < R; ++j) {       // sample order
-      const int n = m + j;
-      const bool valid = n < N, old = n < n1;
-      float& rj = slot<MODEL, R>(r, j);
-      const float rr = valid ? rj : 0.0f;
-      const float e = rr * rr;
-      if (old) so += e; else sn += e;
-      rj = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
+      for (int i = 0; i < R / 2; i += 2) {
+        acc0 = __ffma2_rn(r[i], r[i], acc0);
+        acc1 = __ffma2_rn(r[i + 1], r[i + 1], acc1);
+        r[i] = __fmul2_rn(r[i], w);
+        r[i + 1] = __fmul2_rn(r[i + 1], w);
+      }
+      sn = (acc0.x + acc0.y) + (acc1.x + acc1.y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {     // sample order
+        const int n = m + j;
+        const bool valid = n < N, old = n < n1;
+        float& rj = slot<MODEL, R>(r, j);
+        const float rr = valid ? rj : 0.0f;
+        const float e = rr * rr;
+        if (old) so += e; else sn += e;
+        rj = rr * (old ? inv_s2_f : beta_f * inv_s2_f);
+      }
     }
     kahan_add(eo_s, eo_c, so);
     kahan_add(en_s, en_c, sn);
