@@ -642,12 +642,12 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       de_c = (CT)de;
     }
     if (l >= 0) {   // leapfrog: half step in momentum, full step in position
-      if (warp == 0) {
+      // (the mixed path applies it element by element inside the evaluation's setup)
+      if (PREC == FP64 && warp == 0) {
         for (int i = lane; i < n; i += 32) {
           const CT ph = p1[i] + (CT)0.5 * de_c * g1[i];
           p1[i] = ph;
-          if (PREC == FP64) z1[i] = z1[i] + de * (double)minv[i % D] * (double)ph;
-          else z1[i] = z1[i] + (double)(de_c * minv[i % D] * ph);
+          z1[i] = z1[i] + de * (double)minv[i % D] * (double)ph;
         }
       }
       if (l > 0 && tid == blockDim.x - 1) {   // the leaf's uniform, off the control path
@@ -655,9 +655,15 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
                              (uint64_t)((nsub - 1) + l));
         s_uleaf = u01(w.w[0]);
       }
-      __syncthreads();
+      if (PREC == FP64) __syncthreads();
     }
-    block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+    if constexpr (PREC == MIXED) {
+      const LeapPre leap{p1, g1, z1, minv, de_c};
+      block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr,
+                                                  l >= 0 ? &leap : nullptr);
+    } else {
+      block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
+    }
     if (tid == 0) cs_done += sm.scal[3];
     if (l < 0) {   // initial point: momentum, H0 and both trajectory ends
       if (warp == 0) {

@@ -1079,9 +1079,20 @@ __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, d
 // only for the sinusoid frequency map and phase constants and the final scalars.
 // The serial parts run one thread per (component, parameter) where they can.
 // ---------------------------------------------------------------------------
+// Leapfrog step folded into the mixed setup (NUTS): element i's thread applies the
+// momentum half step p_i += eps/2 g_i and the position step z_i += eps minv p_i before it
+// maps z_i, with the arithmetic of the separate update (FP32 control, FP64 positions).
+struct LeapPre {
+  float* p1;
+  const float* g1;
+  double* z1;
+  const float* minv;
+  float de_c;
+};
+
 template <int MODEL, int R>
 __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const double* z,
-                                  EvalSmem& sm) {
+                                  EvalSmem& sm, const LeapPre* leap = nullptr) {
   constexpr int D = model_d<MODEL>();
   float lp = 0.f;
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
@@ -1093,6 +1104,11 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   // (1) one thread per (component, parameter): coordinate map, Jacobian, prior terms
   for (int i = threadIdx.x; i < KD; i += blockDim.x) {
     const int d = i % D;
+    if (leap) {
+      const float ph = leap->p1[i] + 0.5f * leap->de_c * leap->g1[i];
+      leap->p1[i] = ph;
+      leap->z1[i] = leap->z1[i] + (double)(leap->de_c * leap->minv[d] * ph);
+    }
     const double zi = z[i];
     if (MODEL == PULSE && d > 0) {
       // centre and width to ~1e-12 relative in double-float (FP32 pipe, no FP64)
@@ -1151,11 +1167,12 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
 
 template <int MODEL, int R, bool GRAD, bool FISHER, typename GT>
 __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
-                                 const double* z, EvalSmem& sm, GT* grad_out, double* fis_out) {
+                                 const double* z, EvalSmem& sm, GT* grad_out, double* fis_out,
+                                 const LeapPre* leap = nullptr) {
   constexpr int D = model_d<MODEL>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nw = blockDim.x >> 5;
-  const float lp_t = eval_setup_mixed<MODEL, R>(pb, pa, K, z, sm);
+  const float lp_t = eval_setup_mixed<MODEL, R>(pb, pa, K, z, sm, leap);
 
   // sample indices fit 32 bits (capacity < 2^24): no 64-bit integer work or
   // 64-bit conversions (which issue on the FP64 pipe) inside the sample loop
@@ -1436,9 +1453,10 @@ __device__ __forceinline__ double eval_setup(const ProbDev& pb, const PriorArgs&
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER, typename GT = double>
 __device__ __forceinline__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K,
                                            double beta, const double* z, EvalSmem& sm,
-                                           GT* grad_out, double* fis_out) {
+                                           GT* grad_out, double* fis_out,
+                                           const LeapPre* leap = nullptr) {
   if constexpr (PREC == MIXED)
-    block_eval_mixed<MODEL, R, GRAD, FISHER, GT>(pb, pa, K, beta, z, sm, grad_out, fis_out);
+    block_eval_mixed<MODEL, R, GRAD, FISHER, GT>(pb, pa, K, beta, z, sm, grad_out, fis_out, leap);
   else
     block_eval_fp64<MODEL, PREC, R, GRAD, FISHER>(pb, pa, K, beta, z, sm, grad_out, fis_out);
 }
