@@ -205,8 +205,6 @@ SmemPlan smem_plan(Ctx* c, bool fisher, int depth) {
   sp.nw = c->T / 32;
   sp.depth = depth;
   sp.fisher = fisher;
-  const int span = 32 * c->R;
-  sp.nwr = c->cfg.precision == TSMC_MIXED ? (int)((c->nmax + span - 1) / span) : 0;
   sp.nch = c->cfg.channels == 2 ? 2 : 1;
   return sp;
 }

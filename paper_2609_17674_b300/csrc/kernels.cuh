@@ -37,11 +37,10 @@ struct SmemPlan {
   int nw;          // warps per block
   int depth;       // NUTS checkpoint levels (0 for non-NUTS kernels)
   bool fisher;
-  int nwr;         // warp ranges of the longest problem (active-component masks)
   int nch;         // data channels (mixed-path constants per channel)
   __host__ __device__ size_t eval_bytes() const {
     return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4 + 64) +
-           sizeof(float) * (size_t)kd * NCF * nch + sizeof(uint32_t) * 2 * (size_t)nwr + 32;
+           sizeof(float) * (size_t)kd * NCF * nch + 32;
   }
   __host__ __device__ size_t nuts_bytes() const {
     return sizeof(double) * (size_t)kd * (14 + 2 * (size_t)(depth + 1));   // 8-byte slots
@@ -71,8 +70,7 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
   if (reinterpret_cast<uintptr_t>(d) & 8) d += 1;   // float4 loads of the constants
   sm.cf = reinterpret_cast<float*>(d);
   sm.cfch = sp.kd * NCF;
-  sm.wmask = reinterpret_cast<uint32_t*>(sm.cf + (size_t)sp.kd * NCF * sp.nch);
-  p = reinterpret_cast<char*>(sm.wmask + 2 * (size_t)sp.nwr);
+  p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kd * NCF * sp.nch);
   // keep 8-byte alignment for what follows
   p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
   sm.tw = tw;
@@ -118,7 +116,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) 
   const int K = min(max(io.K[gi], 0), kp.kmax);   // caller array: clamp to the slots
   const double beta = io.beta[prob];
   const double* z = io.z + gi * (int64_t)sp.kd;
-  if (PREC == MIXED) init_block_tables(sm, sp.nwr);
+  if (PREC == MIXED) init_block_tables(sm);
   __syncthreads();
   block_eval<MODEL, PREC, R, GRAD, FISHER>(pb, kp.pa, K, beta, z, sm, gbuf, fbuf);
   const int tid = threadIdx.x;
@@ -304,7 +302,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   EvalSmem sm = carve_eval(p, sp, kp.tw);
   double* zs = reinterpret_cast<double*>(p);    // [kd + D]
   const double* zg = kp.z + gi * (int64_t)sp.kd;
-  if (PREC == MIXED) init_block_tables(sm, sp.nwr);
+  if (PREC == MIXED) init_block_tables(sm);
   for (int i = tid; i < K * D; i += blockDim.x) zs[i] = zg[i];
   if (move == 1 && tid < D) zs[K * D + tid] = s_znew[tid];
   __syncthreads();
@@ -603,7 +601,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (tid < 4) s_minv[tid] = (CT)kp.minv[4 * prob + tid];
   const CT* minv = s_minv;
   const double* zg = kp.z + gi * (int64_t)kd;
-  if (PREC == MIXED) init_block_tables(sm, sp.nwr);
+  if (PREC == MIXED) init_block_tables(sm);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
   double cs_done = 0.0;   // component*samples computed (thread 0)

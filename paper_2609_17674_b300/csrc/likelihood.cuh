@@ -506,7 +506,6 @@ struct EvalSmem {
   double* scal;   // [4]: logp, ll_old, ll_new, component*samples computed
   const double* tw;  // LINAMP fixed (t0, w) [kmax][2] (global)
   float2* exptab;    // mixed path: 2^(j/64), j < 64, as double-float (filled per block)
-  uint32_t* wmask;   // mixed pulse path: [warp ranges][2] bits of the components active there
   // mixed path: FP32 views of the same storage
   __device__ float* fth() const { return reinterpret_cast<float*>(th); }
   __device__ float* fdth() const { return reinterpret_cast<float*>(dth); }
@@ -590,9 +589,8 @@ __device__ __forceinline__ void fill_exp_table(float2* tab) {
 // per-block tables of the mixed path, at kernel start (before the first __syncthreads):
 // the 2^(j/64) table and cleared active-component masks (every evaluation leaves them
 // cleared again)
-__device__ __forceinline__ void init_block_tables(EvalSmem& sm, int nwr) {
+__device__ __forceinline__ void init_block_tables(EvalSmem& sm) {
   fill_exp_table(sm.exptab);
-  for (int i = threadIdx.x; i < 2 * nwr; i += blockDim.x) sm.wmask[i] = 0u;
 }
 
 // e^x as double-float for x in [-80, 80], FP32 arithmetic only (table-driven method of
@@ -1098,9 +1096,6 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
   const int KD = K * D;
   float* th_lo = th + KD;       // double-float low parts of the pulse centre and width
-  const bool win = MODEL != SINUSOID && pa.window;
-  const int span = 32 * R;                      // samples per warp range
-  const int nwr = ((int)pb.n + span - 1) / span;   // masks arrive cleared
   // (1) one thread per (component, parameter): coordinate map, Jacobian, prior terms
   for (int i = threadIdx.x; i < KD; i += blockDim.x) {
     const int d = i % D;
@@ -1135,7 +1130,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
     }
   }
   __syncthreads();
-  // (2) one thread per component: path constants and the warp ranges it reaches
+  // (2) one thread per component: path constants
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     float* cf = sm.cf + k * NCF;
     if (MODEL == SINUSOID) {
@@ -1152,13 +1147,6 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       cf[11] = A / w;                                 // gradient factor A / w
     } else {
       pulse_prep32(th[k * D], sm.tw[2 * k], sm.tw[2 * k + 1], pb, cf);
-    }
-    if (win) {
-      const float lo = fmaxf(cf[9], 0.0f), hi = fminf(cf[10], (float)(pb.n - 1));
-      if (lo <= hi) {
-        const int r0 = (int)lo / span, r1 = min((int)hi / span, nwr - 1);
-        for (int q = r0; q <= r1; ++q) atomicOr(&sm.wmask[2 * q + (k >> 5)], 1u << (k & 31));
-      }
     }
   }
   __syncthreads();
@@ -1219,12 +1207,18 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     const float mf = (float)(m - ch * (int)pb.nc);
     const float* cfb = sm.cf + ch * sm.cfch;
     const float rch = pb.f_resp[2 * ch];
-    // components active on this warp's range, ascending (all K without the window)
+    // components active on this warp's range, ascending (all K without the window):
+    // lanes test components lane and lane + 32 against the range's first and last sample
+    // (the support bounds cf[9], cf[10] are whole sample indices)
     uint32_t act[2];
     if (win) {
-      const int q = wfirst / (32 * R);
-      act[0] = sm.wmask[2 * q];
-      act[1] = sm.wmask[2 * q + 1];
+      const float first = (float)wfirst, last = (float)min(wfirst + 32 * R - 1, N - 1);
+      bool a0 = false, a1 = false;
+      if (lane < K) a0 = !(last < sm.cf[lane * NCF + 9] || first > sm.cf[lane * NCF + 10]);
+      if (lane + 32 < K)
+        a1 = !(last < sm.cf[(lane + 32) * NCF + 9] || first > sm.cf[(lane + 32) * NCF + 10]);
+      act[0] = __ballot_sync(0xffffffffu, a0);
+      act[1] = __ballot_sync(0xffffffffu, a1);
     } else {
       act[0] = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
       act[1] = K >= 64 ? 0xffffffffu : (K > 32 ? ((1u << (K - 32)) - 1u) : 0u);
@@ -1433,10 +1427,6 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     sm.scal[1] = lo;
     sm.scal[2] = ln;
     sm.scal[3] = (double)cnt;
-  }
-  if (win) {   // every warp has left the sample loop (barrier above): clear for the next use
-    const int nwr = (N + 32 * R - 1) / (32 * R);
-    for (int i = tid; i < 2 * nwr; i += blockDim.x) sm.wmask[i] = 0u;
   }
   __syncthreads();
 }
