@@ -594,3 +594,33 @@ def test_two_channel_response_matters():
         wl.resp = resp
         other = oracle.Oracle(wl).logl_grad(z, K, 1.0)["ll_new"][0]
         assert other < base - 10.0
+
+
+@pytest.mark.parametrize("which", ["pulse", "sinusoid", "two_channel"])
+def test_rj_incremental_likelihood_equals_fresh_evaluation(which):
+    """The birth/death move updates ll_old / ll_new by its incremental Delta logL (sum of
+    r h - h^2/2 over the samples, per channel); after every accepted move the carried values
+    must equal a fresh evaluation of the new state."""
+    if which == "pulse":
+        wl = synth.pulse_workload("t", 1500, 3, 6, 1, 77)
+        o = oracle.Oracle(wl, n=1500, n1=600)
+    elif which == "sinusoid":
+        wl = synth.sinusoid_workload("t", 4096, 3, 6, 1, 78)
+        o = oracle.Oracle(wl)
+    else:
+        wl = synth.ae_workload("t", 2048, 3, 6, 1, 79, noise=True)
+        o = oracle.Oracle(wl)
+    z, K = synth.prior_population(wl, 12, 300)
+    beta = 0.4
+    r = o.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    accepted = 0
+    for rnd in range(3):
+        out = o.rj_move(5, rnd, beta, z, K, lo, ln)
+        fresh = o.logl_grad(z, K, beta)
+        acc = (out == 1) | (out == 2)
+        accepted += int(acc.sum())
+        np.testing.assert_allclose(ln[acc], fresh["ll_new"][acc], rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(lo[acc], fresh["ll_old"][acc], rtol=1e-9, atol=1e-9)
+        lo, ln = fresh["ll_old"].copy(), fresh["ll_new"].copy()
+    assert accepted > 20
