@@ -15,7 +15,7 @@ import numpy as np
 
 from . import capi, sampler, synth
 
-CANDIDATES = ((128, 32), (64, 32), (256, 32), (128, 16))
+CANDIDATES = ((128, 32), (96, 32), (64, 32), (256, 32), (128, 16))
 _cache: dict = {}
 
 
