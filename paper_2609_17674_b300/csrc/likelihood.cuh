@@ -1331,6 +1331,9 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
   DF e_o = warp_sum_df(DF{eo_s, -eo_c});
   DF e_n = warp_sum_df(DF{en_s, -en_c});
   DF e_p = warp_sum_df(DF{lp_t, 0.f});
+  // a coordinate beyond the FP32 range has log prior -inf, which the double-float sum
+  // would turn into NaN (inf - inf in its error term): such a warp takes the plain sum
+  if (__any_sync(0xffffffffu, !isfinite(lp_t))) e_p = DF{warp_sum(lp_t), 0.f};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xffffffffu, done, o);
   float* rf = reinterpret_cast<float*>(sm.red);
@@ -1414,16 +1417,19 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
   // ---- block totals, part 2: the last thread, beside the component loop ----
   if (tid == blockDim.x - 1) {
     DF a{0.f, 0.f}, b{0.f, 0.f}, c{0.f, 0.f};
+    float cp = 0.f;   // plain sum of the log prior's warp totals (the non-finite case)
     long long cnt = 0;
     for (int w = 0; w < nw; ++w) {
       a = df_add(a, DF{rf[w * 6 + 0], rf[w * 6 + 1]});
       b = df_add(b, DF{rf[w * 6 + 2], rf[w * 6 + 3]});
       c = df_add(c, DF{rf[w * 6 + 4], rf[w * 6 + 5]});
+      cp += rf[w * 6 + 4];
       cnt += ri[w];
     }
     const double lo = -0.5 * df_to_double(a) * pb.inv_s2;
     const double ln = -0.5 * df_to_double(b) * pb.inv_s2;
-    sm.scal[0] = lo + beta * ln + df_to_double(c);
+    const double lp = isfinite(cp) ? df_to_double(c) : (double)cp;
+    sm.scal[0] = lo + beta * ln + lp;
     sm.scal[1] = lo;
     sm.scal[2] = ln;
     sm.scal[3] = (double)cnt;

@@ -257,6 +257,64 @@ def test_nuts_mixed_agrees_with_oracle():
     np.testing.assert_allclose(acc.cpu().numpy()[same], acc_o[same], rtol=1e-3, atol=1e-6)
 
 
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_extreme_coordinates_stay_finite(prec):
+    """z = +-1e308 puts theta on a prior bound with log prior -1e308 (FP64; the oracle's
+    value) or -inf (mixed: |z| is beyond the FP32 range).  The likelihood and gradient stay
+    those of the bound, a mixed-path NUTS transition from such a point diverges at its first
+    leaf and leaves it in place, the extreme coordinates are never moved, and no NaN reaches
+    the population through a whole SMC stage."""
+    t = torch()
+    wl = synth.pulse_workload("t", 1024, 3, 10, 64, 91)
+    z, K = population(wl, 7, 64, include_edges=False)
+    K[:4] = np.maximum(K[:4], 1)
+    ext = [(0, 0, 1, 1e308), (1, 0, 2, -1e308), (2, 0, 0, 1e308), (3, 0, 1, -1e308)]
+    for i, k, d, v in ext:
+        z[i, k, d] = v
+    beta = 0.3
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, beta)
+    bt = dev_tensor([beta], t.float64)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, bt, grad=True)
+    lo, ln, lp, g = (x.cpu().numpy() for x in (lo, ln, lp, g))
+    res = oracle.Oracle(wl).logl_grad(z, K, beta)
+    tol = TOL[prec]
+    np.testing.assert_allclose(ln, res["ll_new"], rtol=tol)
+    assert np.all(np.isfinite(g))
+    for i, k, d, v in ext:
+        assert g[i, k, d] == pytest.approx(-np.sign(v), rel=1e-6)
+    if prec == capi.FP64:
+        np.testing.assert_allclose(lp, res["logp"], rtol=tol)
+    else:
+        assert np.all(lp[:4] == -np.inf)
+        np.testing.assert_allclose(lp[4:], res["logp"][4:], rtol=tol)
+    eps = [0.05]
+    ctx.set_kernel_params(eps, np.ones((1, wl.D)))
+    acc = t.zeros(64, dtype=t.float64, device="cuda")
+    nl = t.zeros(64, dtype=t.int32, device="cuda")
+    fl = t.zeros(64, dtype=t.int32, device="cuda")
+    ctx.nuts_move(2, 0, acc, nl, fl)
+    zg, Kg, lo_g, ln_g = (x.cpu().numpy() for x in ctx.get_population())
+    assert not np.any(np.isnan(zg)) and np.all(np.isfinite(ln_g)) and np.all(np.isfinite(lo_g))
+    assert np.all(np.isfinite(acc.cpu().numpy()))
+    for i, k, d, v in ext:
+        assert zg[i, k, d] == v
+    if prec == capi.MIXED:
+        assert np.all(fl.cpu().numpy()[:4] & 1)
+        np.testing.assert_array_equal(zg[:4], z[:4])
+        assert np.all(acc.cpu().numpy()[:4] == 0.0)
+    assert np.mean(nl.cpu().numpy()[4:] > 0) > 0.5     # the other particles moved
+    ctx.rj_move(2, 1)
+    ctx.update_metric()
+    _, minv = ctx.get_kernel_params()
+    assert np.all(np.isfinite(minv)) and np.all(minv > 0)
+    ctx.run_stage(3, use_graph=False)
+    zg, Kg, lo_g, ln_g = (x.cpu().numpy() for x in ctx.get_population())
+    assert not np.any(np.isnan(zg))
+    assert np.all(np.isfinite(ln_g)) and np.all(np.isfinite(lo_g))
+    b, lz, ess = ctx.temper_state()
+    assert np.all(np.isfinite(b)) and np.all(np.isfinite(lz)) and np.all(np.isfinite(ess))
+
+
 def test_temper_and_resample_parity():
     wl = synth.config1()
     wl.P = 512

@@ -624,3 +624,35 @@ def test_rj_incremental_likelihood_equals_fresh_evaluation(which):
         np.testing.assert_allclose(lo[acc], fresh["ll_old"][acc], rtol=1e-9, atol=1e-9)
         lo, ln = fresh["ll_old"].copy(), fresh["ll_new"].copy()
     assert accepted > 20
+
+
+def test_extreme_coordinates_saturate():
+    """At |z| = 1e308 the logistic map puts theta on a prior bound: likelihood and gradient
+    equal those at |z| = 800 (where s(z) already rounds to 0 or 1 in FP64), the coordinate's
+    log prior density -|z| - 2 log(1 + e^-|z|) is -1e308, and its z-gradient is -sign(z)
+    (the likelihood's term carries dtheta/dz = s (1 - s) = 0)."""
+    wl = synth.config1()
+    o = oracle.Oracle(wl)
+    rng = np.random.default_rng(1)
+    z = np.zeros((4, wl.kmax, 3))
+    z[:, :2] = rng.standard_normal((4, 2, 3))
+    K = np.full(4, 2, np.int32)
+    z[1] = z[0]
+    z[3] = z[2]
+    z[0, 0, 1], z[1, 0, 1] = 1e308, 800.0
+    z[2, 0, 2], z[3, 0, 2] = -1e308, -800.0
+    r = o.logl_grad(z, K, 0.4)
+    assert np.all(np.isfinite(r["grad"])) and np.all(np.isfinite(r["ll_new"]))
+    for a, b in ((0, 1), (2, 3)):
+        assert r["ll_new"][a] == r["ll_new"][b] and r["ll_old"][a] == r["ll_old"][b]
+        np.testing.assert_array_equal(r["grad"][a], r["grad"][b])
+    assert r["grad"][0, 0, 1] == -1.0 and r["grad"][2, 0, 2] == 1.0
+    assert r["logp"][0] == -1e308 and r["logp"][2] == -1e308
+    # moving that coordinate from 0 to 800 changes its log density from -2 log 2 to -800
+    # (log1p(e^-800) = 0), on top of the tempered likelihood's change
+    z0 = z[1:2].copy()
+    z0[0, 0, 1] = 0.0
+    r0 = o.logl_grad(z0, K[:1], 0.4)
+    dl = (r["ll_old"][1] - r0["ll_old"][0]) + 0.4 * (r["ll_new"][1] - r0["ll_new"][0])
+    assert r["logp"][1] - r0["logp"][0] == pytest.approx(dl - 800.0 + 2.0 * math.log(2.0),
+                                                         rel=1e-12, abs=1e-9)
