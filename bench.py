@@ -35,9 +35,9 @@ OPS_PER_CS = {0: 9.0, 1: 14.0}   # algorithmic FP32 lane-ops per component*sampl
 FP32_LANES_PER_SM = 128
 N_SM = 148
 # DRAM bytes (read + write) per particle of one NUTS launch, from an ncu capture of the
-# same kernel on a 1024-particle launch of this workload (573 KB / 1024 particles);
+# same kernel on a 1024-particle launch of this workload (571 KB / 1024 particles);
 # traffic scales with the particle count (z rows in and out; the samples stay in L2)
-NUTS_DRAM_BYTES_PER_PARTICLE = 559.5
+NUTS_DRAM_BYTES_PER_PARTICLE = 557.75
 
 
 def _args():
