@@ -24,6 +24,9 @@
  *   - Errors: argument errors return TSMC_EINVAL synchronously; CUDA launch
  *     errors return TSMC_ECUDA.  A non-finite target density is not an error
  *     (it means probability zero: the move is rejected / the subtree diverges).
+ *     A particle whose coordinates give a non-finite likelihood or Gauss-Newton
+ *     diagonal (a NaN coordinate) is left out of the metric and gets weight zero
+ *     at the next reweighting, so resampling drops it.
  *     tsmc_last_error gives a one-line message for the last failure.
  *   - One context per host thread; contexts are independent.
  */
@@ -182,7 +185,8 @@ tsmc_status tsmc_get_birth_proposal(void* ctx, int32_t problem, double* out_host
 
 /* Metric from the population (Sec. 3.2, mass matrix = Hessian of -log target):
  * minv_d = 1 / max(1e-8, mean over particles and active components of the
- * Gauss-Newton diagonal at the current beta). */
+ * Gauss-Newton diagonal at the current beta; particles with a non-finite diagonal
+ * are left out). */
 tsmc_status tsmc_update_metric(void* ctx);
 
 /* Choose beta by ESS bisection, reweight (evidence increment) and resample

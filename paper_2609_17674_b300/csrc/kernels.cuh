@@ -887,7 +887,11 @@ __global__ void __launch_bounds__(1024) k_temper(TemperIO io, int P) {
     delta = lo > 0.0 ? lo : hi;
     ess_sums(ell, P, m, delta, red, s1, s2);
   }
-  for (int i = threadIdx.x; i < P; i += blockDim.x) logw[i] = delta * ell[i];
+  // a particle whose likelihood is not finite has zero weight, as in the ESS sums
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double e = ell[i];
+    logw[i] = isfinite(e) ? delta * e : -INFINITY;
+  }
   if (threadIdx.x == 0) {
     io.beta[prob] = to_one ? 1.0 : beta + delta;
     io.logz[prob] += (delta * m + log(s1)) - log((double)P);
@@ -974,7 +978,11 @@ __global__ void __launch_bounds__(1024) k_temper_mixed(TemperIO io, int P, float
   }
   double s1, s2;
   ess_sums(ell, P, m, delta, red, s1, s2);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) logw[i] = delta * ell[i];
+  // a particle whose likelihood is not finite has zero weight, as in the ESS sums
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double e = ell[i];
+    logw[i] = isfinite(e) ? delta * e : -INFINITY;
+  }
   if (threadIdx.x == 0) {
     io.beta[prob] = to_one ? 1.0 : beta + delta;
     io.logz[prob] += (delta * m + log(s1)) - log((double)P);
@@ -1076,6 +1084,9 @@ __global__ void k_metric(const double* fis_sum, const int32_t* K, const ProbDev*
   double v[5] = {0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     const int64_t g = (int64_t)prob * P + i;
+    bool fin = true;
+    for (int d = 0; d < D; ++d) fin = fin && isfinite(fis_sum[g * D + d]);
+    if (!fin) continue;   // a particle with a non-finite coordinate has zero density
     for (int d = 0; d < D; ++d) v[d] += fis_sum[g * D + d];
     v[4] += (double)K[g];
   }

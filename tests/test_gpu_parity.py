@@ -315,6 +315,49 @@ def test_extreme_coordinates_stay_finite(prec):
     assert np.all(np.isfinite(b)) and np.all(np.isfinite(lz)) and np.all(np.isfinite(ess))
 
 
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_nan_particle_has_zero_density(prec):
+    """A particle with a NaN coordinate has a NaN likelihood (zero density): its NUTS
+    transition diverges at the first leaf, it does not enter the population metric (which
+    equals the metric with that particle's K set to 0), it gets zero weight at the next
+    reweighting, and after one SMC stage no NaN is left in the population."""
+    t = torch()
+    wl = synth.pulse_workload("t", 1024, 3, 10, 64, 92)
+    z, K = population(wl, 8, 64, include_edges=False)
+    K[5] = max(K[5], 1)
+    z[5, 0, 1] = np.nan
+    beta = 0.2
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, beta)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([beta], t.float64), grad=True)
+    ln, lp = ln.cpu().numpy(), lp.cpu().numpy()
+    assert np.isnan(ln[5]) and np.isnan(lp[5])
+    others = np.arange(64) != 5
+    res = oracle.Oracle(wl).logl_grad(z[others], K[others], beta)
+    np.testing.assert_allclose(ln[others], res["ll_new"], rtol=TOL[prec])
+    ctx.update_metric()
+    _, minv = ctx.get_kernel_params()
+    K0 = K.copy()
+    K0[5] = 0
+    ctx0, _, _ = context_with_population(wl, prec, z, K0, beta)
+    ctx0.update_metric()
+    _, minv0 = ctx0.get_kernel_params()
+    assert np.all(np.isfinite(minv))
+    np.testing.assert_array_equal(minv, minv0)
+    acc = t.zeros(64, dtype=t.float64, device="cuda")
+    nl = t.zeros(64, dtype=t.int32, device="cuda")
+    fl = t.zeros(64, dtype=t.int32, device="cuda")
+    ctx.nuts_move(2, 0, acc, nl, fl)
+    assert fl.cpu().numpy()[5] & 1 and acc.cpu().numpy()[5] == 0.0
+    zg = ctx.get_population()[0].cpu().numpy()
+    assert np.isnan(zg[5, 0, 1]) and not np.any(np.isnan(np.delete(zg, 5, axis=0)))
+    b, lz, ess = ctx.run_stage(3, use_graph=False)
+    zg, Kg, lo_g, ln_g = (x.cpu().numpy() for x in ctx.get_population())
+    anc = ctx.get_ancestors().cpu().numpy()
+    assert 5 not in anc
+    assert not np.any(np.isnan(zg)) and np.all(np.isfinite(ln_g)) and np.all(np.isfinite(lo_g))
+    assert np.all(np.isfinite(b)) and np.all(np.isfinite(lz)) and np.all(np.isfinite(ess))
+
+
 def test_temper_and_resample_parity():
     wl = synth.config1()
     wl.P = 512
