@@ -1,4 +1,6 @@
-"""Segment experiment of the paper's pulse example (Sec. 5.1, prior-start against
+"""Experiments on the sampler.
+
+Segment experiment of the paper's pulse example (Sec. 5.1, prior-start against
 posterior-start): data arrive in segments, each 20 s longer than the last.
 
 - prior-start: every segment is analysed from the prior (bridge Eq. prior_bridge);
@@ -7,6 +9,10 @@ posterior-start): data arrive in segments, each 20 s longer than the last.
 
 Reported per segment: SMC stages to reach beta = 1, log Z (increments summed along the
 posterior-start chain), the posterior over K and the wall time.
+
+Also: the population birth proposal against prior births, and the throughput of the batched
+logL + gradient evaluation per precision (``python -m paper_2609_17674_b300.experiments eval
+--precision fp64``, one JSON line).
 """
 from __future__ import annotations
 
@@ -134,3 +140,62 @@ def birth_proposal_comparison(wl: Workload, mid_stages: int = 12, rounds: int = 
                 mid_stage=mid_stages, mid_beta=float(beta[0]), proposal_centres=m_built,
                 outcomes_differing=int(np.sum(outs[0] != outs[1])),
                 birth_acceptance_prior=acc[0], birth_acceptance_population=acc[1])
+
+
+def eval_throughput(wl: Workload, precision: int, reps: int = 3, seed: int = 1,
+                    beta: float = 0.5, pulse_window: int = 1) -> dict:
+    """Batched logL + gradient over a prior population of the workload (K_p N counted per
+    particle): one warm-up launch, then the best of reps launches timed with CUDA events on
+    the context's stream."""
+    import torch
+
+    from . import synth
+
+    z, K = synth.prior_population(wl, seed)
+    nb = len(wl.problems)
+    stream = torch.cuda.Stream()
+    zd = torch.as_tensor(z, device="cuda")
+    Kd = torch.as_tensor(K, device="cuda")
+    bt = torch.full((nb,), beta, dtype=torch.float64, device="cuda")
+    ctx = sampler.open_context(wl, precision, stream=stream, pulse_window=pulse_window)
+    ctx.set_population(zd, Kd, beta=[beta] * nb)
+    g = torch.empty_like(zd)
+    with torch.cuda.stream(stream):
+        ctx.eval(zd, Kd, bt, grad=True, g=g)
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.eval(zd, Kd, bt, grad=True, g=g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    ctx.close()
+    cs = float(K.astype(np.int64).sum()) * wl.problems[0].n
+    return dict(workload=wl.name, precision="fp64" if precision == capi.FP64 else "mixed",
+                ms_per_launch=best, cs_per_s=cs / (best * 1e-3))
+
+
+def _main(argv=None):
+    import argparse
+    import json
+
+    from . import synth
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2609_17674_b300.experiments")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    ev = sub.add_parser("eval", help="batched logL + gradient throughput (pulse workload)")
+    ev.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ev.add_argument("--particles", type=int, default=8192)
+    ev.add_argument("--samples", type=int, default=16384)
+    ev.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    wl = synth.config2(P=a.particles, n=a.samples)
+    prec = capi.FP64 if a.precision == "fp64" else capi.MIXED
+    print(json.dumps(eval_throughput(wl, prec, reps=a.reps)))
+
+
+if __name__ == "__main__":
+    _main()
