@@ -257,18 +257,22 @@ def test_nuts_mixed_agrees_with_oracle():
     np.testing.assert_allclose(acc.cpu().numpy()[same], acc_o[same], rtol=1e-3, atol=1e-6)
 
 
+@pytest.mark.parametrize("model", ["pulse", "sinusoid"])
 @pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
-def test_extreme_coordinates_stay_finite(prec):
+def test_extreme_coordinates_stay_finite(prec, model):
     """z = +-1e308 puts theta on a prior bound with log prior -1e308 (FP64; the oracle's
     value) or -inf (mixed: |z| is beyond the FP32 range).  The likelihood and gradient stay
     those of the bound, a mixed-path NUTS transition from such a point diverges at its first
     leaf and leaves it in place, the extreme coordinates are never moved, and no NaN reaches
     the population through a whole SMC stage."""
     t = torch()
-    wl = synth.pulse_workload("t", 1024, 3, 10, 64, 91)
+    if model == "pulse":
+        wl = synth.pulse_workload("t", 1024, 3, 10, 64, 91)
+    else:
+        wl = synth.sinusoid_workload("t", 4096, 3, 6, 64, 93)
     z, K = population(wl, 7, 64, include_edges=False)
     K[:4] = np.maximum(K[:4], 1)
-    ext = [(0, 0, 1, 1e308), (1, 0, 2, -1e308), (2, 0, 0, 1e308), (3, 0, 1, -1e308)]
+    ext = [(0, 0, 1, 1e308), (1, 0, 2, -1e308), (2, 0, 0, 1e308), (3, 0, wl.D - 1, -1e308)]
     for i, k, d, v in ext:
         z[i, k, d] = v
     beta = 0.3
