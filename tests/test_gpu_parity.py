@@ -202,6 +202,65 @@ def test_nuts_parity_fp64():
     assert np.mean(nl_o) > 3  # the trees were non-trivial
 
 
+def test_sinusoid_rj_parity_fp64():
+    """Single-channel sinusoids (FP64 path): a birth/death move with the oracle's outcomes,
+    K, z and carried likelihoods."""
+    t = torch()
+    wl = synth.sinusoid_workload("t", 1024, 2, 4, 96, 47)
+    ora = oracle.Oracle(wl)
+    z, K = population(wl, 14, 96)
+    beta = 0.35
+    ctx, _, _ = context_with_population(wl, capi.FP64, z, K, beta)
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo, Ko = z.copy(), K.copy()
+    out_o = ora.rj_move(6, 1, beta, zo, Ko, lo, ln)
+    outd = t.zeros(96, dtype=t.int32, device="cuda")
+    ctx.rj_move(6, 1, outd)
+    zg, Kg, _, lng = ctx.get_population()
+    assert np.array_equal(outd.cpu().numpy(), out_o)
+    assert np.array_equal(Kg.cpu().numpy(), Ko)
+    np.testing.assert_allclose(zg.cpu().numpy(), zo, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(lng.cpu().numpy(), ln, rtol=1e-10)
+    assert len(np.unique(out_o)) >= 3
+
+
+@pytest.mark.parametrize("eps", [0.5, 1.0])
+def test_sinusoid_nuts_parity_fp64(eps):
+    """Single-channel sinusoids (FP64 path) near the injection: one NUTS transition with the
+    oracle's leaf counts, depth and divergence flags, end points and acceptance statistics
+    (eps 0.5: U-turns at depths 2-6; eps 1.0: divergences as well)."""
+    t = torch()
+    wl = synth.sinusoid_workload("t", 1024, 2, 4, 96, 47)
+    ora = oracle.Oracle(wl)
+    beta = 0.35
+    rng = np.random.default_rng(5)
+    zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+    K = np.full(96, 2, np.int32)
+    z = np.zeros((96, 4, 4))
+    z[:, :2] = zt[None] + 0.002 * rng.standard_normal((96, 2, 4))
+    minv = ora.metric(z, K, beta)
+    ctx, _, _ = context_with_population(wl, capi.FP64, z, K, beta)
+    ctx.set_kernel_params([eps], minv[None, :])
+    acc = t.zeros(96, dtype=t.float64, device="cuda")
+    nl = t.zeros(96, dtype=t.int32, device="cuda")
+    fl = t.zeros(96, dtype=t.int32, device="cuda")
+    ctx.nuts_move(3, 2, acc, nl, fl)
+    zg, _, _, ln_g = ctx.get_population()
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo = z.copy()
+    acc_o, nl_o, fl_o = ora.nuts_move(3, 2, beta, eps, minv, zo, K, lo, ln)
+    assert np.array_equal(nl.cpu().numpy(), nl_o)
+    assert np.array_equal(fl.cpu().numpy(), fl_o)
+    np.testing.assert_allclose(zg.cpu().numpy(), zo, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(acc.cpu().numpy(), acc_o, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(ln_g.cpu().numpy(), ln, rtol=1e-10)
+    assert len(np.unique(fl_o >> 8)) >= 3
+    if eps == 1.0:
+        assert np.any(fl_o & 1)
+
+
 def test_nuts_mixed_moves_and_stays_finite():
     t = torch()
     wl = synth.config2(P=256, n=16384)
