@@ -90,6 +90,42 @@ def test_linamp_eval_and_fisher(prec):
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_linamp_nuts_parity(prec):
+    """Linear-amplitude model (fixed centres and widths, Gaussian amplitude prior): one NUTS
+    transition against the oracle; FP64: the same trees (leaf counts, depths) and end
+    points; mixed: the same trees for almost every particle."""
+    t = torch()
+    wl = synth.linamp_workload(n=512, k=3, P=64, seed=33)
+    ora = oracle.Oracle(wl)
+    rng = np.random.default_rng(4)
+    z = rng.normal(1.0, 1.0, (64, 3, 1))
+    K = np.full(64, 3, np.int32)
+    beta, eps = 0.5, 0.02
+    minv = ora.metric(z, K, beta)
+    ctx, _, _ = context_with_population(wl, prec, z, K, beta)
+    ctx.set_kernel_params([eps], minv[None, :])
+    acc = t.zeros(64, dtype=t.float64, device="cuda")
+    nl = t.zeros(64, dtype=t.int32, device="cuda")
+    fl = t.zeros(64, dtype=t.int32, device="cuda")
+    ctx.nuts_move(2, 0, acc, nl, fl)
+    zg = ctx.get_population()[0].cpu().numpy()
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo = z.copy()
+    acc_o, nl_o, fl_o = ora.nuts_move(2, 0, beta, eps, minv, zo, K, lo, ln)
+    assert len(np.unique(fl_o >> 8)) >= 4
+    if prec == capi.FP64:
+        assert np.array_equal(nl.cpu().numpy(), nl_o)
+        assert np.array_equal(fl.cpu().numpy(), fl_o)
+        np.testing.assert_allclose(zg, zo, rtol=1e-9, atol=1e-9)
+    else:
+        same = (nl.cpu().numpy() == nl_o) & (fl.cpu().numpy() == fl_o)
+        assert np.mean(same) >= 0.9, np.mean(same)
+        close = np.all(np.isclose(zg, zo, rtol=1e-4, atol=1e-5), axis=(1, 2))
+        assert np.mean(close[same]) >= 0.9, np.mean(close[same])
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
 @pytest.mark.parametrize("model", ["pulse", "sinusoid"])
 def test_fisher_parity(prec, model):
     t = torch()
