@@ -19,6 +19,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 PULSE, SINUSOID, PULSE_LINAMP = 0, 1, 2
 FP64, MIXED = 0, 1
+SCHED_ROUNDS, SCHED_MIXTURE = 0, 1
 
 # every entry point declared in include/tsmc.h, with its ctypes signature
 P, I32, I64, D, U32, U64, SZ = (C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint32,

@@ -57,3 +57,80 @@ def test_create_rejects_misaligned_workspace_without_device_work():
     h = C.c_void_p()
     assert L.tsmc_create(C.byref(cfg), cap.ctypes.data, 0x1001, 1 << 30, None, C.byref(h)) == capi.EINVAL
     assert L.tsmc_create(C.byref(cfg), cap.ctypes.data, 0x100000, 16, None, C.byref(h)) == capi.ENOMEM
+
+
+def _ws_status(cfg, n):
+    cap = np.array([n], dtype=np.int64)
+    nb = C.c_size_t(0)
+    return capi.lib().tsmc_workspace_bytes(C.byref(cfg), cap.ctypes.data, C.byref(nb))
+
+
+# (workload, field, value, expected status): every rule of the configuration check, with the
+# values just inside each bound accepted
+_PULSE = synth.config1
+_AE = lambda: synth.ae_workload("t", 1024, 2, 4, 16, 1)   # noqa: E731
+CFG_CASES = [
+    (_PULSE, "model", 3, capi.EINVAL),
+    (_PULSE, "precision", 2, capi.EINVAL),
+    (_PULSE, "n_problems", 0, capi.EINVAL),
+    (_PULSE, "particles", 0, capi.EINVAL),
+    (_PULSE, "kmin", -1, capi.EINVAL),
+    (_PULSE, "kmin", 11, capi.EINVAL),          # above kmax = 10
+    (_PULSE, "kmin", 10, capi.OK),
+    (_PULSE, "max_depth", 0, capi.EINVAL),
+    (_PULSE, "max_depth", 10, capi.OK),
+    (_PULSE, "n_mut", -1, capi.EINVAL),
+    (_PULSE, "alpha", 0.0, capi.EINVAL),
+    (_PULSE, "alpha", 1.5, capi.EINVAL),
+    (_PULSE, "alpha", 1.0, capi.OK),
+    (_PULSE, "threads", 16, capi.EINVAL),
+    (_PULSE, "threads", 288, capi.EINVAL),
+    (_PULSE, "threads", 256, capi.OK),
+    (_PULSE, "threads", 32, capi.OK),
+    (_PULSE, "samples_per_thread", 8, capi.EINVAL),
+    (_PULSE, "samples_per_thread", 16, capi.OK),
+    (_PULSE, "pulse_window", 2, capi.EINVAL),
+    (_PULSE, "birth_proposal", 2, capi.EINVAL),
+    (_PULSE, "channels", 2, capi.EINVAL),       # two channels are for sinusoids only
+    (_PULSE, "channels", 3, capi.EINVAL),
+    (_AE, "channels", 2, capi.OK),
+]
+
+
+@pytest.mark.parametrize("mk,field,value,want", CFG_CASES)
+def test_config_rules(mk, field, value, want):
+    wl = mk()
+    cfg = make_config(wl, capi.MIXED)
+    setattr(cfg, field, value)
+    assert _ws_status(cfg, wl.problems[0].n) == want
+
+
+def test_config_rules_birth_proposal_and_response():
+    wl = synth.config1()
+    cfg = make_config(wl, capi.MIXED)
+    cfg.birth_proposal = 1
+    for w, want in ((0.0, capi.EINVAL), (1.5, capi.EINVAL), (float("nan"), capi.EINVAL),
+                    (1.0, capi.OK), (0.1, capi.OK)):
+        cfg.birth_prior_weight = w
+        assert _ws_status(cfg, 1024) == want, w
+    ae = synth.ae_workload("t", 1024, 2, 4, 16, 1)
+    for q, v in ((0, 0.0), (2, -1.0), (1, float("inf")), (3, float("nan"))):
+        cfg = make_config(ae, capi.MIXED)
+        cfg.response[q] = v
+        assert _ws_status(cfg, 1024) == capi.EINVAL, (q, v)
+    cfg = make_config(ae, capi.MIXED)
+    cfg.schedule = capi.SCHED_ROUNDS     # birth and death both needed in every round
+    cfg.p_birth = 0.0
+    assert _ws_status(cfg, 1024) == capi.EINVAL
+
+
+def test_make_config_maps_the_workload():
+    ae = synth.ae_workload("t", 1024, 2, 4, 16, 1)
+    cfg = make_config(ae, capi.FP64)
+    assert cfg.channels == 2 and cfg.model == capi.SINUSOID
+    assert list(cfg.response) == pytest.approx(list(ae.resp))
+    pw = synth.paper_pulse_workload(P=600)
+    cfg = make_config(pw, capi.MIXED)
+    assert cfg.kmin == 1 and cfg.kmax == pw.kmax and cfg.particles == 600
+    assert cfg.schedule == capi.SCHED_MIXTURE     # the paper's mixture of moves
+    assert cfg.alpha == pytest.approx(0.9)
