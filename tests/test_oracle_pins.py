@@ -393,6 +393,43 @@ def test_smc_evidence_and_posterior_match_linear_gaussian_closed_form():
     assert np.all(np.abs(mu.mean(0) - mean) < 4 * sem)
 
 
+def _linamp_log_evidence(wl, nn):
+    """Closed-form log p(d_0..d_{nn-1}) of the linear-Gaussian model, without the Gaussian
+    normalisation -nn/2 log(2 pi sigma^2) that the sampler leaves out of its moves."""
+    pr = wl.problems[0]
+    t = np.arange(pr.n)[:nn] / pr.n
+    G = np.exp(-((t[:, None] - wl.fixed_tw[None, :, 0]) ** 2) / (2 * wl.fixed_tw[None, :, 1] ** 2))
+    s2 = pr.sigma**2
+    S = s2 * np.eye(nn) + wl.amp_sd**2 * G @ G.T
+    r = pr.d[:nn] - G @ np.full(wl.kmax, wl.amp_mean)
+    _, logdet = np.linalg.slogdet(S)
+    return -0.5 * r @ np.linalg.solve(S, r) - 0.5 * logdet + 0.5 * nn * math.log(s2)
+
+
+def test_assimilation_evidence_matches_linear_gaussian_closed_form():
+    """Posterior start (Sec. 4): SMC on the first n1 samples, then, from its particles, a run
+    that tempers in the remaining samples (old samples at weight 1, new ones at beta).  The
+    first run's evidence must match log p(d_old) and the second's the increment
+    log p(d_new | d_old) = log p(d) - log p(d_old), both in closed form."""
+    n, n1, P = 256, 128, 400
+    wl0 = synth.linamp_workload(n=n, k=3, P=P, seed=31)
+    exact_old = _linamp_log_evidence(wl0, n1)
+    exact_inc = _linamp_log_evidence(wl0, n) - exact_old
+    lz_old, lz_inc = [], []
+    for seed in range(6):
+        wl = synth.linamp_workload(n=n, k=3, P=P, seed=31)
+        wl.seed = 200 + seed
+        r1 = oracle.Oracle(wl, n=n1).smc_run(P)
+        r2 = oracle.Oracle(wl, n=n, n1=n1).smc_run(P, init_prior=False, z=r1["z"], K=r1["K"],
+                                                   stage0=r1["n_stages"])
+        assert r1["beta"][-1] == 1.0 and r2["beta"][-1] == 1.0
+        lz_old.append(r1["logz"])
+        lz_inc.append(r2["logz"])
+    for lz, exact in ((np.array(lz_old), exact_old), (np.array(lz_inc), exact_inc)):
+        se = max(lz.std(ddof=1) / math.sqrt(len(lz)), 0.01)
+        assert abs(lz.mean() - exact) < 3 * se + 0.02, (lz.mean(), exact, se)
+
+
 # --------------------------------------------------------------------------
 # Tempering and resampling
 # --------------------------------------------------------------------------
