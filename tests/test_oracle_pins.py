@@ -269,6 +269,32 @@ def test_rj_converges_to_k_prior_at_beta_zero():
     assert stats.kstest(zz, "logistic").pvalue > 1e-3
 
 
+def test_mixture_schedule_keeps_the_prior_at_beta_zero():
+    """Mixture schedule (every round each particle draws NUTS, birth or death) with unequal
+    birth and death probabilities: the acceptance ratio carries log(p_death / p_birth), so at
+    beta = 0 a population drawn from the prior stays there (K ~ U{0..kmax}, z ~ logistic).
+    Without that term, or with its sign flipped, K drifts to a bound by 0.2 per round.  The
+    three move types occur with their probabilities."""
+    wl = synth.pulse_workload("t", 8, 1, 5, 1, 1)
+    wl.schedule, wl.p_nuts, wl.p_birth, wl.p_death = 1, 0.5, 0.35, 0.15
+    o = oracle.Oracle(wl)
+    P = 4000
+    z, K = synth.prior_population(wl, 3, P)
+    lo, ln = np.zeros(P), np.zeros(P)
+    types = np.zeros(3)
+    for rnd in range(60):
+        st, r = rnd // 16, rnd % 16
+        out = o.rj_move(st, r, 0.0, z, K, lo, ln)
+        types += [np.sum(out == 0), np.sum(np.abs(out) == 1), np.sum(np.abs(out) == 2)]
+        o.nuts_move(st, r, 0.0, 0.8, np.ones(4), z, K, lo, ln)
+    assert stats.chisquare(np.bincount(K, minlength=6)).pvalue > 1e-3
+    zz = np.concatenate([z[i, : K[i]].ravel() for i in range(P)])
+    assert stats.kstest(zz, "logistic").pvalue > 1e-3
+    n = types.sum()
+    for f, p in zip(types / n, (0.5, 0.35, 0.15)):
+        assert abs(f - p) < 5 * math.sqrt(p * (1 - p) / n)
+
+
 def test_rj_with_lower_bound_keeps_k_prior_at_beta_zero():
     """K prior U{kmin..kmax} (the paper's pulse example uses [1, 10]): started at K = kmin,
     birth/death at beta = 0 reaches the uniform prior on {kmin..kmax} and never leaves it;
