@@ -652,6 +652,32 @@ def test_mixture_schedule_stage_matches_oracle_fp64():
     assert np.mean(close[same]) > 0.9
 
 
+def test_mixture_schedule_unequal_birth_death_rj_parity_fp64():
+    """Mixture schedule with p_birth != p_death (0.35 / 0.15), where the acceptance's
+    log(p_death / p_birth) term does not vanish: one birth/death round with the oracle's
+    move types, outcomes, K, z and likelihoods."""
+    t = torch()
+    wl = synth.pulse_workload("t", 1500, 3, 6, 200, 77)
+    wl.schedule = synth.SCHED_MIXTURE
+    wl.p_nuts, wl.p_birth, wl.p_death = 0.5, 0.35, 0.15
+    z, K = population(wl, 15, 200)
+    beta = 0.02
+    ora = oracle.Oracle(wl)
+    ctx, _, _ = context_with_population(wl, capi.FP64, z, K, beta)
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo, Ko = z.copy(), K.copy()
+    out_o = ora.rj_move(4, 1, beta, zo, Ko, lo, ln)
+    outd = t.zeros(200, dtype=t.int32, device="cuda")
+    ctx.rj_move(4, 1, outd)
+    zg, Kg, _, lng = ctx.get_population()
+    assert np.array_equal(outd.cpu().numpy(), out_o)
+    assert np.array_equal(Kg.cpu().numpy(), Ko)
+    np.testing.assert_allclose(zg.cpu().numpy(), zo, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(lng.cpu().numpy(), ln, rtol=1e-10)
+    assert set(np.unique(out_o)) >= {0, 1, -1, 2}
+
+
 @pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
 def test_linear_gaussian_evidence_on_gpu(prec):
     """SMC log Z and posterior mean against the closed form of the linear-Gaussian model."""
