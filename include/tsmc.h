@@ -96,7 +96,10 @@ typedef struct {
 
 /* Workspace size for a configuration and per-problem sample capacities
  * n_capacity_host[n_problems] (the largest N each problem will hold, including
- * assimilated samples).  The workspace must be 256-byte aligned device memory. */
+ * assimilated samples; both channels' samples for channels = 2).  Each capacity must be
+ * in [1, 2^24]: sample indices are exact in FP32 and fit 32-bit arithmetic in the
+ * sample loops; otherwise TSMC_EINVAL.  The workspace must be 256-byte aligned device
+ * memory. */
 tsmc_status tsmc_workspace_bytes(const tsmc_config* cfg, const int64_t* n_capacity_host,
                                  size_t* bytes);
 

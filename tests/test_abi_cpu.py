@@ -134,3 +134,11 @@ def test_make_config_maps_the_workload():
     assert cfg.kmin == 1 and cfg.kmax == pw.kmax and cfg.particles == 600
     assert cfg.schedule == capi.SCHED_MIXTURE     # the paper's mixture of moves
     assert cfg.alpha == pytest.approx(0.9)
+
+
+def test_sample_capacity_bounds():
+    """Capacities in [1, 2^24] (sample indices exact in FP32 and 32-bit in the loops)."""
+    cfg = make_config(synth.config1(), capi.MIXED)
+    for n, want in ((1, capi.OK), (1 << 24, capi.OK), ((1 << 24) + 1, capi.EINVAL),
+                    (0, capi.EINVAL)):
+        assert _ws_status(cfg, n) == want, n
