@@ -224,7 +224,7 @@ def config4(seed=1004, P=16384, n_full=1 << 19) -> Workload:
 # The paper's own pulse example (Sec. 5.1): 10 Gaussian pulses in 200 s of noise-free data,
 # uniform priors on (A, mu, width) that also serve as the birth proposal, K in [1, 10],
 # 6000 particles, alpha = 0.9, mixture moves NUTS / birth / death = 0.6 / 0.2 / 0.2, and data
-# arriving in segments 20 s longer each time.  Not given there (readings): 10 samples per
+# arriving in segments 20 s longer each time.  Not given there, so chosen here: 10 samples per
 # second, a likelihood sigma of 0.05, A in [0.5, 2], width in [1, 6] s, and the injected
 # values below (one pulse near 150 s, as in its segment-count discussion).
 PAPER_PULSE_LO = (0.5, 0.0, 1.0, 0.0)
