@@ -60,7 +60,7 @@ def _args():
 def workload(rank: int, P: int, n: int):
     from paper_2609_17674_b300 import dist as tdist, synth
 
-    return synth.config2(seed=tdist.rank_seed(1002, rank), P=P, n=n)
+    return synth.pulse_k20(seed=tdist.rank_seed(1002, rank), P=P, n=n)
 
 
 # ---------------------------------------------------------------------------
@@ -72,7 +72,7 @@ def _oracle_worker(args):
     import oracle
     from paper_2609_17674_b300 import synth
 
-    wl = synth.config2(seed=wl_seed, P=P, n=n)
+    wl = synth.pulse_k20(seed=wl_seed, P=P, n=n)
     o = oracle.Oracle(wl)
     z, K = synth.prior_population(wl, 7)
     z, K = z[idx].copy(), K[idx].copy()
@@ -218,7 +218,7 @@ def measure_extras(stream):
 
     out = {}
     # (1) batched logL+grad kernel, pulse N=16384, K_max=40, P=8192, prior population
-    wl = synth.config2()
+    wl = synth.pulse_k20()
     z, K = synth.prior_population(wl, 1)
     zd, Kd = torch.as_tensor(z, device="cuda"), torch.as_tensor(K, device="cuda")
     beta = torch.tensor([0.5], dtype=torch.float64, device="cuda")
@@ -239,7 +239,7 @@ def measure_extras(stream):
                                **thr, "mixed_over_fp64": thr["mixed"] / thr["fp64"],
                                "mixed_no_window_over_fp64": thr["mixed_no_window"] / thr["fp64"]}
     # (2) full SMC, N=1024 pulses, FP64 vs mixed, against the 20-run oracle reference
-    gold = os.path.join(ROOT, "tests", "golden", "smc_config1_oracle.json")
+    gold = os.path.join(ROOT, "tests", "golden", "smc_pulse_n1024_oracle.json")
     if os.path.exists(gold):
         runs = _json.load(open(gold))["runs"]
         gh = np.array([r["hist"] for r in runs])
@@ -248,7 +248,7 @@ def measure_extras(stream):
         for name, prec in (("fp64", capi.FP64), ("mixed", capi.MIXED)):
             hs, zs, ts = [], [], []
             for seed in range(4):
-                w1 = synth.config1()
+                w1 = synth.pulse_n1024_k3()
                 w1.seed = seed
                 ctx = sampler.open_context(w1, prec, stream=stream)
                 torch.cuda.synchronize()
@@ -290,7 +290,7 @@ def measure_extras(stream):
                                "nuts_transition": cna / (msn * 1e-3), "nuts_ms": msn}
     ctx.close()
     # (3) 64 independent GB bands (N_b 2^14..2^18, P=2048 each) in one launch
-    w5 = synth.config5()
+    w5 = synth.gb_bands()
     nb = len(w5.problems)
     best = autotune.tune(w5, capi.MIXED, nuts=False)
     ctx = sampler.open_context(w5, capi.MIXED, stream=stream, threads=best["threads"],

@@ -192,7 +192,7 @@ def _main(argv=None):
     ev.add_argument("--samples", type=int, default=16384)
     ev.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
-    wl = synth.config2(P=a.particles, n=a.samples)
+    wl = synth.pulse_k20(P=a.particles, n=a.samples)
     prec = capi.FP64 if a.precision == "fp64" else capi.MIXED
     print(json.dumps(eval_throughput(wl, prec, reps=a.reps)))
 

@@ -196,24 +196,24 @@ def sinusoid_workload(name, n, k_true, kmax, P, seed, **kw) -> Workload:
 
 
 # ---------------------------------------------------------------------------
-# The five workloads (data seed 1000 + index)
+# The five benchmark workloads (data seeds 1001 to 1005)
 # ---------------------------------------------------------------------------
-def config1(seed=1001) -> Workload:
+def pulse_n1024_k3(seed=1001) -> Workload:
     """Gaussian-pulse sum, N=1024 on [0,1], K_true=3, sigma=0.1, K~U{0..10}, P=512."""
     return pulse_workload("pulse_n1024_k3_p512", 1024, 3, 10, 512, seed)
 
 
-def config2(seed=1002, P=8192, n=16384) -> Workload:
+def pulse_k20(seed=1002, P=8192, n=16384) -> Workload:
     """Gaussian-pulse sum at scale: N=16384, K_true=20, K_max=40, P=8192."""
     return pulse_workload(f"pulse_n{n}_k20_p{P}", n, 20, 40, P, seed)
 
 
-def config3(seed=1003, P=4096, n=1 << 18) -> Workload:
+def gb_band_k10(seed=1003, P=4096, n=1 << 18) -> Workload:
     """Galactic-binary band: N=2^18 at dt=15 s, sigma=1, K_true=10, K_max=30, P=4096."""
     return sinusoid_workload(f"gb_n{n}_k10_p{P}", n, 10, 30, P, seed)
 
 
-def config4(seed=1004, P=16384, n_full=1 << 19) -> Workload:
+def assimilation_pulse_k14(seed=1004, P=16384, n_full=1 << 19) -> Workload:
     """Assimilation: pulses on t_n = n/2^19, K_true=14, data arrive as 2^17, 2^18, 2^19."""
     rng = _rng(seed)
     pr = pulse_problem(rng, n_full, 14, 0.1, span_n=n_full)
@@ -248,7 +248,7 @@ def paper_pulse_workload(P=6000, seed=2001, rate=10.0, sigma=0.05, n_mut=5) -> W
                     seed=seed, kmin=1)
 
 
-def config5(seed=1005, n_bands=64, P=2048, log2n=(14, 18)) -> Workload:
+def gb_bands(seed=1005, n_bands=64, P=2048, log2n=(14, 18)) -> Workload:
     """64 independent GB bands with disjoint 5 uHz windows, N_b = round(2^U[14,18])."""
     rng = _rng(seed)
     probs = []

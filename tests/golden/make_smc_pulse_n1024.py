@@ -1,11 +1,11 @@
-"""Writes smc_config1_oracle.json: 20 oracle SMC runs on the N=1024 pulse workload.
+"""Writes smc_pulse_n1024_oracle.json: 20 oracle SMC runs on the N=1024 pulse workload.
 
 Calls only the oracle (and the shared input generator).  Each run is a prior-start
 SMC (P=512, K ~ U{0..10}, alpha=0.5, 5 rounds of RJ + NUTS per stage) with Philox
 seed s; the data are the same for every run.  Stored per run: the K histogram of
 the final population, log Z, the stage count, and label-invariant summaries
 (mean K; mean sorted pulse centres and amplitudes for particles with K = K_true).
-Run:  python tests/golden/make_smc_config1.py   (about 5 minutes on 8 cores)
+Run:  python tests/golden/make_smc_pulse_n1024.py   (about 5 minutes on 8 cores)
 """
 import json
 import multiprocessing as mp
@@ -41,7 +41,7 @@ def run(seed):
     import oracle
     from paper_2609_17674_b300 import synth
 
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.seed = seed
     res = oracle.Oracle(wl).smc_run(wl.P, max_stages=400)
     s = summaries(wl, res["z"], res["K"])
@@ -58,6 +58,6 @@ if __name__ == "__main__":
         runs = pool.map(run, range(20))
     out = {"workload": "pulse_n1024_k3_p512 (data seed 1001), Philox seeds 0..19",
            "runs": runs}
-    with open(os.path.join(HERE, "smc_config1_oracle.json"), "w") as f:
+    with open(os.path.join(HERE, "smc_pulse_n1024_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", len(runs), "runs")

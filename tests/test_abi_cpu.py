@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_workspace_bytes_and_config_validation():
     L = capi.lib()
-    wl = synth.config2()
+    wl = synth.pulse_k20()
     cfg = make_config(wl, capi.MIXED)
     cap = np.array([wl.problems[0].n], dtype=np.int64)
     nb = C.c_size_t(0)
@@ -51,7 +51,7 @@ def test_workspace_bytes_and_config_validation():
 
 def test_create_rejects_misaligned_workspace_without_device_work():
     L = capi.lib()
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     cfg = make_config(wl, capi.FP64)
     cap = np.array([1024], dtype=np.int64)
     h = C.c_void_p()
@@ -67,7 +67,7 @@ def _ws_status(cfg, n):
 
 # (workload, field, value, expected status): every rule of the configuration check, with the
 # values just inside each bound accepted
-_PULSE = synth.config1
+_PULSE = synth.pulse_n1024_k3
 _AE = lambda: synth.ae_workload("t", 1024, 2, 4, 16, 1)   # noqa: E731
 CFG_CASES = [
     (_PULSE, "model", 3, capi.EINVAL),
@@ -106,7 +106,7 @@ def test_config_rules(mk, field, value, want):
 
 
 def test_config_rules_birth_proposal_and_response():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     cfg = make_config(wl, capi.MIXED)
     cfg.birth_proposal = 1
     for w, want in ((0.0, capi.EINVAL), (1.5, capi.EINVAL), (float("nan"), capi.EINVAL),
@@ -138,7 +138,7 @@ def test_make_config_maps_the_workload():
 
 def test_sample_capacity_bounds():
     """Capacities in [1, 2^24] (sample indices exact in FP32 and 32-bit in the loops)."""
-    cfg = make_config(synth.config1(), capi.MIXED)
+    cfg = make_config(synth.pulse_n1024_k3(), capi.MIXED)
     for n, want in ((1, capi.OK), (1 << 24, capi.OK), ((1 << 24) + 1, capi.EINVAL),
                     (0, capi.EINVAL)):
         assert _ws_status(cfg, n) == want, n

@@ -75,7 +75,7 @@ def test_rj_move_with_proposal_matches_oracle_fp64(pop):
 
 
 def test_smc_stages_with_proposal_match_oracle_fp64():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.P = 128
     wl.birth_proposal, wl.birth_prior_weight = 1, 0.3
     ctx = sampler.open_context(wl, capi.FP64)
@@ -112,17 +112,17 @@ def test_rj_move_with_proposal_mixed_agrees():
 def test_smc_with_population_births_reaches_the_oracle_posterior():
     """Twenty mixed-path runs of the N=1024 pulse workload with births from the population
     mixture against the twenty oracle runs with births from the prior
-    (tests/golden/smc_config1_oracle.json): the proposal changes the path, not the target,
+    (tests/golden/smc_pulse_n1024_oracle.json): the proposal changes the path, not the target,
     so the K histogram, log Z and the parameter summaries agree within 3 standard errors."""
     here = os.path.dirname(__file__)
-    gold = json.load(open(os.path.join(here, "golden", "smc_config1_oracle.json")))["runs"]
+    gold = json.load(open(os.path.join(here, "golden", "smc_pulse_n1024_oracle.json")))["runs"]
     spec = importlib.util.spec_from_file_location(
-        "mk", os.path.join(here, "golden", "make_smc_config1.py"))
+        "mk", os.path.join(here, "golden", "make_smc_pulse_n1024.py"))
     mk = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mk)
     runs = []
     for r0 in gold:
-        wl = synth.config1()
+        wl = synth.pulse_n1024_k3()
         wl.seed = r0["seed"]
         wl.birth_proposal, wl.birth_prior_weight = 1, 0.2
         ctx = sampler.open_context(wl, capi.MIXED)

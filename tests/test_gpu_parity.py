@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_philox_matches_oracle():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     ctx = sampler.open_context(wl, capi.FP64)
     rng = np.random.default_rng(3)
     ctr = rng.integers(0, 2**63, size=(64, 4), dtype=np.uint64)
@@ -141,7 +141,7 @@ def test_fisher_parity(prec, model):
 
 @pytest.mark.parametrize("kmin", [0, 1])
 def test_init_population_matches_oracle(kmin):
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.P = 300
     wl.kmin = kmin
     ctx = sampler.open_context(wl, capi.FP64)
@@ -187,7 +187,7 @@ def test_rj_move_parity_fp64(n1, kmin):
 
 def test_rj_move_mixed_agrees():
     t = torch()
-    wl = synth.config2(P=512, n=16384)
+    wl = synth.pulse_k20(P=512, n=16384)
     z, K = population(wl, 21, 512)
     ora = oracle.Oracle(wl)
     ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.01)
@@ -306,7 +306,7 @@ def test_sinusoid_nuts_parity(prec, eps):
 
 def test_nuts_mixed_moves_and_stays_finite():
     t = torch()
-    wl = synth.config2(P=256, n=16384)
+    wl = synth.pulse_k20(P=256, n=16384)
     z, K = population(wl, 2, 256)
     ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.001)
     ctx.update_metric()
@@ -465,7 +465,7 @@ def test_nan_particle_has_zero_density(prec):
 
 
 def test_temper_and_resample_parity():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.P = 512
     ctx = sampler.open_context(wl, capi.FP64)
     ctx.init_population()
@@ -495,7 +495,7 @@ def test_metric_parity():
 def test_stage_graph_matches_eager():
     res = []
     for graph in (False, True):
-        wl = synth.config1()
+        wl = synth.pulse_n1024_k3()
         wl.P = 256
         ctx = sampler.open_context(wl, capi.FP64)
         ctx.init_population()
@@ -512,7 +512,7 @@ def test_stage_graph_matches_eager():
 
 def test_smc_stage_matches_oracle_fp64():
     """One full stage (temper, resample, metric, RJ + NUTS rounds) on both sides."""
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.P = 128
     wl.n_mut = 2
     ctx = sampler.open_context(wl, capi.FP64)
@@ -535,7 +535,7 @@ def test_smc_stage_matches_oracle_fp64():
 def test_full_size_pulse_sampled(prec):
     """N=16384, K_max=40, P=8192 in the benchmark launch configuration; oracle on a sample."""
     t = torch()
-    wl = synth.config2()
+    wl = synth.pulse_k20()
     z, K = population(wl, 1, wl.P)
     ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.25)
     bt = dev_tensor([0.25], t.float64)
@@ -550,7 +550,7 @@ def test_full_size_pulse_sampled(prec):
 def test_full_size_sinusoid_sampled(prec):
     """N=2^18 Galactic-binary band, K_max=30, P=4096; oracle on a sample of particles."""
     t = torch()
-    wl = synth.config3()
+    wl = synth.gb_band_k10()
     z, K = population(wl, 1, wl.P)
     zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
     for i in range(2, 40, 2):
@@ -570,7 +570,7 @@ def test_full_size_assimilation_sampled():
     """N=2^19 samples, P=16384, K_max=40: the largest configuration, with the second half
     of the data new (tempered) and the first half assimilated; oracle on a sample."""
     t = torch()
-    wl = synth.config4()
+    wl = synth.assimilation_pulse_k14()
     n = wl.problems[0].n
     z, K = population(wl, 4, wl.P)
     ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.3, n_use=n, n1=n // 2)
@@ -597,7 +597,7 @@ def test_autograd_function_backward():
 
 
 def test_bad_arguments_rejected():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     ctx = sampler.open_context(wl, capi.FP64)
     with pytest.raises(capi.TsmcError):
         ctx.set_problem(0, np.array([1.0, np.nan]), 0.0, 1.0, 0.1, synth.PULSE_LO, synth.PULSE_HI, 4)
@@ -614,7 +614,7 @@ def test_bad_arguments_rejected():
 def test_pulse_window_matches_full_evaluation():
     """The support window changes nothing beyond FP32 resolution and skips real work."""
     t = torch()
-    wl = synth.config2(P=256)
+    wl = synth.pulse_k20(P=256)
     z, K = population(wl, 4, 256)
     out = []
     for win in (0, 1):
@@ -634,7 +634,7 @@ def test_pulse_window_matches_full_evaluation():
 
 def test_mixture_schedule_stage_matches_oracle_fp64():
     """The paper's kernel mixture (p_NUTS, p_birth, p_death = 0.6, 0.2, 0.2 per round)."""
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.P = 128
     wl.n_mut = 3
     wl.schedule = synth.SCHED_MIXTURE
@@ -712,7 +712,7 @@ def test_linear_gaussian_evidence_on_gpu(prec):
 
 def test_state_errors_and_constant_ell():
     t = torch()
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     cfg = sampler.make_config(wl, capi.FP64)
     ctx = capi.Context(cfg, [1024])
     with pytest.raises(capi.TsmcError, match="error -6"):     # no data yet
@@ -734,7 +734,7 @@ def test_state_errors_and_constant_ell():
 def test_mixed_temper_matches_oracle():
     """The mixed path's FP32 bisection passes choose the same beta as the FP64 definition
     (to the precision of an FP32 ESS) and the FP64 evidence increment."""
-    wl = synth.config2(P=8192)
+    wl = synth.pulse_k20(P=8192)
     z, K = synth.prior_population(wl, 3)
     t = torch()
     ctx = sampler.open_context(wl, capi.MIXED)

@@ -2,7 +2,7 @@
 
 Twenty prior-start runs on the GPU (Philox seeds 0..19, FP64 and mixed paths) are
 compared with twenty oracle runs with the same seeds (tests/golden/
-smc_config1_oracle.json, written by make_smc_config1.py from the oracle alone):
+smc_pulse_n1024_oracle.json, written by make_smc_pulse_n1024.py from the oracle alone):
 the K-posterior histogram, log Z and the label-invariant summaries (sorted pulse
 centres and amplitudes among particles with K = K_true) agree within 3 Monte-Carlo
 standard errors.
@@ -18,7 +18,7 @@ from paper_2609_17674_b300 import capi, sampler, synth
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "smc_config1_oracle.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "smc_pulse_n1024_oracle.json")
 
 
 def _gpu_runs(prec, seeds):
@@ -27,12 +27,12 @@ def _gpu_runs(prec, seeds):
     sys_path = os.path.join(os.path.dirname(__file__), "golden")
     import importlib.util
 
-    spec = importlib.util.spec_from_file_location("mk", os.path.join(sys_path, "make_smc_config1.py"))
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(sys_path, "make_smc_pulse_n1024.py"))
     mk = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mk)
     runs = []
     for s in seeds:
-        wl = synth.config1()
+        wl = synth.pulse_n1024_k3()
         wl.seed = s
         ctx = sampler.open_context(wl, prec)
         out = sampler.run_smc(ctx, max_stages=400)

@@ -49,7 +49,7 @@ def test_ragged_problems_one_stage_match_oracle_fp64():
 def test_batched_bands_full_size_sampled():
     """64 GB bands, N_b from 2^14 to 2^18, 2048 particles each, one launch."""
     t = torch()
-    wl = synth.config5()
+    wl = synth.gb_bands()
     nb = len(wl.problems)
     zs, Ks = [], []
     for b in range(nb):
@@ -72,7 +72,7 @@ def test_batched_bands_full_size_sampled():
 
 def test_assimilate_likelihood_of_new_samples():
     t = torch()
-    wl = synth.config4(P=64, n_full=1 << 14)
+    wl = synth.assimilation_pulse_k14(P=64, n_full=1 << 14)
     pr = wl.problems[0]
     z, K = population(wl, 3, 64)
     n1 = 1 << 12

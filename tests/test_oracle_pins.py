@@ -49,7 +49,7 @@ def _pulse_wl(n, d=None, kmax=2):
 
 
 def test_empty_model_logl_is_data_energy():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     o = oracle.Oracle(wl)
     d = wl.problems[0].d
     r = o.logl_grad(np.zeros((1, wl.kmax, 3)), np.zeros(1, np.int32), 1.0)
@@ -321,7 +321,7 @@ def test_rj_with_lower_bound_keeps_k_prior_at_beta_zero():
 
 
 def test_init_population_with_lower_bound():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     wl.kmin = 1
     z, K = oracle.Oracle(wl).init_population(20000)
     assert K.min() == 1 and K.max() == 10
@@ -477,7 +477,7 @@ def test_temper_two_point_closed_form():
 
 
 def test_resample_properties():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     o = oracle.Oracle(wl)
     P = 512
     assert np.array_equal(o.resample(3, np.zeros(P)), np.arange(P))
@@ -492,7 +492,7 @@ def test_resample_properties():
 
 
 def test_init_population_draws_the_prior():
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     z, K = oracle.Oracle(wl).init_population(22000)
     assert stats.chisquare(np.bincount(K, minlength=11)).pvalue > 1e-3
     zz = np.concatenate([z[i, : K[i]].ravel() for i in range(2000)])
@@ -694,7 +694,7 @@ def test_extreme_coordinates_saturate():
     equal those at |z| = 800 (where s(z) already rounds to 0 or 1 in FP64), the coordinate's
     log prior density -|z| - 2 log(1 + e^-|z|) is -1e308, and its z-gradient is -sign(z)
     (the likelihood's term carries dtheta/dz = s (1 - s) = 0)."""
-    wl = synth.config1()
+    wl = synth.pulse_n1024_k3()
     o = oracle.Oracle(wl)
     rng = np.random.default_rng(1)
     z = np.zeros((4, wl.kmax, 3))
