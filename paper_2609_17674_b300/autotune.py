@@ -11,8 +11,6 @@ from __future__ import annotations
 import json
 import os
 
-import numpy as np
-
 from . import capi, sampler, synth
 
 CANDIDATES = ((128, 32), (96, 32), (64, 32), (256, 32), (128, 16))

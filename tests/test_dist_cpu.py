@@ -1,7 +1,6 @@
 """The weak-scaling bookkeeping of the multi-rank benchmark, on CPU with gloo, 2 ranks."""
 import os
 
-import pytest
 import torch.multiprocessing as mp
 
 from paper_2609_17674_b300 import dist as tdist

@@ -22,8 +22,6 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "smc_pulse_n1024_orac
 
 
 def _gpu_runs(prec, seeds):
-    import torch
-
     sys_path = os.path.join(os.path.dirname(__file__), "golden")
     import importlib.util
 
