@@ -7,7 +7,7 @@
  * No blocking, fusion or reordering beyond the definitions cited per function.
  *
  * Parity status: every function below is pinned by the CPU tests (numpy's
- * Philox, complex-step/finite-difference gradients, closed-form evidence of a
+ * Philox, Richardson finite-difference gradients, closed-form evidence of a
  * linear-Gaussian model, brute-force K posterior, prior invariance of the RJ
  * kernel, leapfrog reversibility, textbook ESS/resampling identities).
  */
@@ -86,6 +86,8 @@ static double logaddexp(double a, double b) {
 /* s(z).  Either way the prior density of z is the logistic density           */
 /* s(z)(1-s(z)), with d/dz log = 1 - 2 s(z) and -d2/dz2 log = 2 s(1-s).        */
 /* LINAMP (linear-Gaussian test model): identity map, A ~ N(amp_mean, sd^2).  */
+/* The paper samples in BlackJAX's unconstrained space (Sec. 4) and does not  */
+/* state the map; this is the reading used throughout.                        */
 /* ------------------------------------------------------------------------- */
 static double logistic(double z) {
   if (z >= 0) return 1.0 / (1.0 + exp(-z));
@@ -128,6 +130,8 @@ static void log_prior_1(const orc_cfg* c, double z, double* lp, double* g, doubl
 /* Templates.  Gaussian pulse h = A exp(-(t-t0)^2/(2w^2)); quasi-monochromatic */
 /* sinusoid h = A cos(2 pi f t + pi fdot t^2 + phi0) with the phase evaluated  */
 /* in the fixed order ((2pi f) t + (pi fdot)(t t)) + phi0.                     */
+/* Pulses: the toy model of Sec. 5.1; sinusoids: the Galactic-binary signal   */
+/* of Sec. 5.2 without the detector response.                                 */
 /* ------------------------------------------------------------------------- */
 double orc_template(const orc_cfg* c, int k, const double* th, double t, double* dh) {
   if (c->model == ORC_PULSE || c->model == ORC_PULSE_LINAMP) {
@@ -179,6 +183,8 @@ double orc_template_ch(const orc_cfg* c, int k, const double* th, double t, int 
 /* dlogL_c/dtheta_kd = sum_n c_n r_n dh_k/dtheta_d / sigma^2, chain rule to z. */
 /* gscale: the same sums of absolute terms (conditioning scale for tests).    */
 /* fisher: Gauss-Newton diagonal sum_n c_n (dh/dz)^2/sigma^2 + prior curvature.*/
+/* Sec. 2: the bridges Eq. prior_bridge and Eq. reuse_bridge; the noise model */
+/* is Eq. gw_likelihood of Sec. 5.2 with a flat PSD, in the time domain.      */
 /* ------------------------------------------------------------------------- */
 #define ORC_MAXKD 256
 void orc_logl_grad(const orc_cfg* c, const orc_data* dat, const double* z, int32_t K, double beta,
@@ -254,6 +260,7 @@ void orc_logl_grad_batch(const orc_cfg* c, const orc_data* dat, const double* z,
 /* Population initialisation (prior start): K ~ U{kmin..kmax}, each coordinate*/
 /* z = logit(u) (so theta ~ its uniform / log-uniform prior); LINAMP: K fixed */
 /* at kmax and A = amp_mean + amp_sd * normal.                                */
+/* The prior start of Sec. 4 (particles drawn from the prior at beta = 0).    */
 /* ------------------------------------------------------------------------- */
 void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z, int32_t* K) {
   const int D = c->D;
@@ -291,6 +298,7 @@ void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z
 /* log alpha_death = dL + log p(K-1) - log p(K) + log p_birth - log p_death;   */
 /* p(K) uniform on {kmin..kmax} so the K-prior terms vanish inside the support.*/
 /* Birth at kmax and death at kmin are rejected.  Acceptance iff log u < log a.*/
+/* Sec. 3.1, Eq. rj_acceptance.                                               */
 /* ------------------------------------------------------------------------- */
 void orc_rj_move_q(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
                    int32_t round, double beta, int32_t P, double* z, int32_t* K,
@@ -480,6 +488,7 @@ void orc_kde_build(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
 /* ------------------------------------------------------------------------- */
 /* Hamiltonian dynamics: H = -logp(z) + 1/2 p^T M^-1 p with diagonal M,        */
 /* leapfrog p += eps/2 grad; z += eps M^-1 p; grad'; p += eps/2 grad'.         */
+/* Sec. 3.2.                                                                  */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   const orc_cfg* c; const orc_data* dat; int32_t K; double beta;
@@ -537,6 +546,7 @@ static double dot_minv(int n, int D, const double* minv, const double* rho, cons
 /* way.  Random numbers: direction (index = depth), leaf selection (index =    */
 /* leaf number in the transition), top-level selection (index = depth),       */
 /* momentum (normal m of the stream).                                          */
+/* Sec. 3.2 (the paper uses BlackJAX's NUTS without stating its variant).     */
 /* ------------------------------------------------------------------------- */
 #define ORC_MAXDEPTH 10
 void orc_nuts_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t stage,
@@ -649,6 +659,8 @@ void orc_nuts_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32
 /* exp(2 LSE(delta ell) - LSE(2 delta ell)); solve ESS = alpha P by bisection  */
 /* on delta in (0, 1-beta], keeping the lower end so that ESS >= alpha P;      */
 /* evidence increment log(1/P sum w_i) = LSE(delta ell) - log P.               */
+/* Sec. 2: Eq. incremental_weight, Eq. ess, Eq. ess_target and the evidence   */
+/* ratio that follows them.                                                   */
 /* ------------------------------------------------------------------------- */
 static double lse_scaled(int32_t P, const double* ell, double s) {
   double m = -INFINITY;
@@ -689,6 +701,7 @@ void orc_temper(int32_t P, const double* ell, double alpha, double beta, double*
 /* ------------------------------------------------------------------------- */
 /* Systematic resampling: W_i = exp(logw_i - max), C its inclusive prefix sum, */
 /* one U ~ (0,1) per (problem, stage); ancestor a_i = min{j : C_j > (i+U)/P C_P}*/
+/* The resampling step of Sec. 2 (its scheme is not stated there).            */
 /* ------------------------------------------------------------------------- */
 void orc_resample(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
                   const double* logw, int32_t* ancestors) {
@@ -716,6 +729,7 @@ void orc_resample(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
 /* Gauss-Newton diagonal per parameter type, floored at 1e-8; minv = 1/M.      */
 /* Step size: eps <- eps exp(mean_acc - 0.8), clamped to [1e-4, 2];            */
 /* eps_0 = 0.5 (kmax D)^(-1/4).                                                */
+/* Sec. 3.2 (mass matrix); the step-size rule is not stated in the paper.     */
 /* ------------------------------------------------------------------------- */
 void orc_metric(const orc_cfg* c, const orc_data* dat, const double* z, const int32_t* K,
                 int32_t P, double beta, double* minv) {
@@ -753,6 +767,8 @@ double orc_eps_initial(const orc_cfg* c) { return 0.5 * pow((double)(c->kmax * c
 /* resample, metric, n_mut rounds of mutation } until beta = 1.  Rounds        */
 /* schedule: each round one RJ move then one NUTS transition; mixture          */
 /* schedule: each round every particle draws NUTS / birth / death.             */
+/* Sec. 4; the mixture is Eq. kernel_mixture of Sec. 3 with the weights of    */
+/* Sec. 5.1.                                                                  */
 /* ------------------------------------------------------------------------- */
 int32_t orc_smc_run(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t P,
                     int32_t init_prior, int32_t stage0, int32_t max_stages, double* eps_io,
