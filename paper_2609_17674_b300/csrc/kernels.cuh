@@ -78,7 +78,8 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
 }
 
 // ---------------------------------------------------------------------------
-// Batched evaluation: one block per particle (caller arrays).
+// Batched evaluation: one block per particle (caller arrays).  The tempered likelihood
+// of the bridges Eq. prior_bridge and Eq. reuse_bridge (Sec. 2) and its gradient.
 // ---------------------------------------------------------------------------
 struct EvalIO {
   const double* z; const int32_t* K; const double* beta;
@@ -143,7 +144,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_eval(KParams kp, EvalIO io, SmemPlan sp) 
 }
 
 // ---------------------------------------------------------------------------
-// Prior initialisation: one thread per particle.
+// Prior initialisation (the prior start of Sec. 4): one thread per particle.
 // ---------------------------------------------------------------------------
 __global__ void k_init(KParams kp, int64_t Ptot) {
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -172,7 +173,8 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
 }
 
 // ---------------------------------------------------------------------------
-// Reversible-jump birth/death: one block per particle (Sec. 3.1 nested map).
+// Reversible-jump birth/death: one block per particle (Sec. 3.1 nested map,
+// Eq. rj_acceptance).
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Population birth proposal (Sec. 6: the particles of a stage approximate its tempered
@@ -495,8 +497,8 @@ __global__ void k_kde_build(KParams kp, int32_t* kcum, double* kde_out, double f
 }
 
 // ---------------------------------------------------------------------------
-// NUTS transition: one block per particle.  Warp 0 runs the tree logic on the
-// (K*D)-vectors in shared memory; every leapfrog calls the block-wide
+// NUTS transition (Sec. 3.2): one block per particle.  Warps 0 and 1 run the tree
+// logic on the (K*D)-vectors in shared memory; every leapfrog calls the block-wide
 // evaluation.  Control values are broadcast through shared memory.
 // ---------------------------------------------------------------------------
 struct NutsOut { double* acc; int32_t* nleaf; int32_t* flags; };
@@ -813,7 +815,8 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
 }
 
 // ---------------------------------------------------------------------------
-// Adaptive tempering (one block per problem): ESS(delta) = (sum x)^2 / sum x^2 with
+// Adaptive tempering (Sec. 2, Eqs. incremental_weight, ess and ess_target; one block
+// per problem): ESS(delta) = (sum x)^2 / sum x^2 with
 // x_i = exp(delta (ell_i - max ell)); bisection for ESS = alpha P on (0, 1-beta].
 // ---------------------------------------------------------------------------
 struct TemperIO {
@@ -991,7 +994,8 @@ __global__ void __launch_bounds__(1024) k_temper_mixed(TemperIO io, int P, float
 }
 
 // ---------------------------------------------------------------------------
-// Systematic resampling (one block per problem): FP64 inclusive scan of
+// Systematic resampling (the resampling step of Sec. 2; one block per problem): FP64
+// inclusive scan of
 // W_i = exp(logw_i - max), U from Philox, a_i = min{j : C_j > (i+U)/P C_P}.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_resample(const double* logw_all, double* cw_all,
@@ -1074,7 +1078,7 @@ __global__ void k_gather(const int32_t* anc, const ProbDev* probs, int P, int kd
 }
 
 // ---------------------------------------------------------------------------
-// Metric and step size (one block per problem)
+// Metric (the mass matrix of Sec. 3.2) and step size (one block per problem)
 // ---------------------------------------------------------------------------
 __global__ void k_metric(const double* fis_sum, const int32_t* K, const ProbDev* probs, int P,
                          int D, double* minv) {

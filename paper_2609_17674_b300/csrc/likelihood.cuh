@@ -16,8 +16,9 @@
 // sample index) and the multiplicative recurrence g_{j+1} = g_j q_j,
 // q_{j+1} = q_j rho (rho = 2^(-2 delta^2)); sinusoids use a double-float phase
 // anchor per thread, reduced mod 2pi with a three-part Cody-Waite split of 2pi,
-// then a rotation recurrence.  Partial sums are FP32 over <= 32 samples and a
-// 5-level warp tree, FP64 above (blocked pairwise summation).
+// then a rotation recurrence.  Mixed-path sums: FP32 over a thread's samples, a warp
+// tree, per-warp Kahan rows across segments and double-float block totals; the FP64
+// path sums in FP64 (blocked pairwise).
 #pragma once
 #include "common.cuh"
 
