@@ -40,3 +40,21 @@ def test_run_smc_respects_max_stages_and_posterior_start():
     assert ctx.inits == 0                            # posterior start: population given
     assert ctx.stages == [0, 1, 2, 3] and out["n_stages"] == 4
     assert out["beta"][-1, 1] < 1.0
+
+
+def test_autotune_reads_its_cache_without_a_device(tmp_path):
+    """A cached launch shape for the workload's key (model, precision, N_max, K_max,
+    P_total) is returned as stored; other keys in the file are ignored."""
+    import json
+
+    from paper_2609_17674_b300 import autotune, capi, synth
+
+    wl = synth.pulse_n1024_k3()
+    key = [wl.model, capi.MIXED, 1024, wl.kmax, wl.P]
+    best = {"threads": 96, "samples_per_thread": 32, "ms": {"96x32": 1.0}}
+    other = {"threads": 256, "samples_per_thread": 16, "ms": {}}
+    f = tmp_path / "tune.json"
+    json.dump([{"key": [wl.model, capi.FP64, 1024, wl.kmax, wl.P], "best": other},
+               {"key": key, "best": best}], open(f, "w"))
+    autotune._cache.clear()
+    assert autotune.tune(wl, capi.MIXED, cache_file=str(f)) == best
