@@ -192,6 +192,90 @@ def test_linamp_fisher_closed_form():
 
 
 # --------------------------------------------------------------------------
+# Metric (Sec. 3.2: the mass matrix is the Hessian of the negative log posterior, read
+# as the population mean of the Gauss-Newton diagonal, floored at 1e-8, then inverted)
+# and the initial step size 0.5 (K_max D)^(-1/4)
+# --------------------------------------------------------------------------
+def _linamp_unequal_widths(n=400, sigma=0.1, amp_sd=0.7):
+    """Linear-amplitude model with three fixed pulses of very different widths, so that the
+    Gauss-Newton diagonal differs by component (it does not depend on the amplitudes)."""
+    t = np.arange(n, dtype=np.float64) / n
+    tw = np.array([[0.2, 0.004], [0.5, 0.03], [0.8, 0.12]])
+    d = 0.05 * np.sin(7.0 * t)
+    pr = synth.Problem(d=d, t_origin=0.0, dt=1.0 / n, sigma=sigma)
+    wl = synth.Workload("linamp_unequal", synth.PULSE_LINAMP, 3, 1, [pr], amp_mean=1.0,
+                        amp_sd=amp_sd, fixed_tw=tw)
+    G = np.exp(-((t[:, None] - tw[None, :, 0]) ** 2) / (2.0 * tw[None, :, 1] ** 2))
+    return wl, G
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.35, 1.0])
+def test_metric_is_inverse_population_mean_of_gauss_newton_diagonal(beta):
+    """orc_metric against the closed form of the linear model: per component
+    F_k = beta sum_n g_k(t_n)^2 / sigma^2 + 1 / s0^2, averaged over every active component
+    of every particle (particles with K = 0 contribute nothing), then inverted.  Dividing by
+    the particle count, counting K = 0 particles, averaging per particle first or returning
+    the mean instead of its inverse each fail here."""
+    wl, G = _linamp_unequal_widths()
+    o = oracle.Oracle(wl)
+    F = beta * np.sum(G * G, 0) / wl.problems[0].sigma ** 2 + 1.0 / wl.amp_sd ** 2
+    K = np.array([3, 0, 1, 2, 0, 1, 3, 1], np.int32)
+    rng = np.random.default_rng(8)
+    z = rng.normal(1.0, 2.0, (K.shape[0], 3, 1))      # amplitudes do not enter F
+    num = sum(F[:k].sum() for k in K)
+    expect = K.sum() / num
+    got = o.metric(z, K, beta)
+    assert got.shape == (1,)
+    assert got[0] == pytest.approx(expect, rel=1e-12)
+    # the three wrong reductions named above give clearly different values
+    assert abs(K.shape[0] / num - expect) > 1e-3 * expect
+    assert abs(np.count_nonzero(K) / num - expect) > 1e-3 * expect
+    if beta > 0.0:   # at beta = 0 every component has the same F (the prior curvature)
+        per_particle = np.mean([F[:k].mean() for k in K if k > 0])
+        assert abs(1.0 / per_particle - expect) > 1e-3 * expect
+
+
+def test_metric_per_parameter_prior_curvature_and_floor():
+    """At beta = 0 with every sample new the likelihood term vanishes, so for the pulse model
+    the diagonal is the logistic prior curvature 2 s(z)(1 - s(z)) of each coordinate; the
+    metric is then 1 / mean over active components, per parameter (coordinates chosen so
+    the three parameters differ: a transposed index fails).  Coordinates at |z| = 30 give a
+    curvature of ~2e-13, below the 1e-8 floor: the metric is 1e8 there."""
+    wl = synth.pulse_workload("t", 256, 2, 4, 4, 3)
+    o = oracle.Oracle(wl)
+    K = np.array([2, 0, 4, 1], np.int32)
+    z = np.zeros((4, 4, 3))
+    rng = np.random.default_rng(2)
+    for i, k in enumerate(K):
+        z[i, :k, 0] = rng.normal(0.0, 0.3, k)
+        z[i, :k, 1] = rng.normal(2.0, 0.3, k)
+        z[i, :k, 2] = rng.normal(-4.0, 0.3, k)
+    s = 1.0 / (1.0 + np.exp(-z))
+    curv = 2.0 * s * (1.0 - s)
+    act = np.arange(4)[None, :] < K[:, None]
+    expect = act.sum() / curv[act].sum(0)
+    np.testing.assert_allclose(o.metric(z, K, 0.0), expect, rtol=1e-12)
+    zf = z.copy()
+    zf[act] = 30.0
+    zf[2] = -30.0
+    np.testing.assert_array_equal(o.metric(zf, K, 0.0), np.full(3, 1e8))
+    # no component anywhere: unit metric
+    np.testing.assert_array_equal(o.metric(z, np.zeros(4, np.int32), 0.0), np.ones(3))
+
+
+def test_initial_step_size_scales_with_total_dimension():
+    """eps_0 = 0.5 (K_max D)^(-1/4): it depends on K_max D only and eps_0^4 K_max D = 1/16."""
+    e = {}
+    for name, wl in (("p40", synth.pulse_workload("t", 64, 2, 40, 4, 1)),
+                     ("s30", synth.sinusoid_workload("t", 64, 2, 30, 4, 1)),
+                     ("p10", synth.pulse_workload("t", 64, 2, 10, 4, 1))):
+        e[name] = oracle.Oracle(wl).eps_initial()
+        assert e[name] ** 4 * wl.kmax * wl.D == pytest.approx(1.0 / 16.0, rel=1e-14)
+    assert e["p40"] == e["s30"]                     # 40 x 3 = 30 x 4 = 120
+    assert e["p10"] / e["p40"] == pytest.approx(4.0 ** 0.25, rel=1e-14)
+
+
+# --------------------------------------------------------------------------
 # Hamiltonian dynamics and NUTS
 # --------------------------------------------------------------------------
 def test_leapfrog_is_reversible():
