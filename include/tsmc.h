@@ -68,7 +68,7 @@ typedef struct {
   double alpha;           /* ESS target fraction, Eq. ess_target */
   double p_nuts, p_birth, p_death;  /* Eq. kernel_mixture; p_birth=p_death=0.5 in ROUNDS */
   double amp_mean, amp_sd;          /* LINAMP Gaussian amplitude prior */
-  uint64_t seed;          /* Philox4x64-10 key word 0 (word 1 = problem index) */
+  uint64_t seed;          /* Philox4x64-10 key word 0 (word 1 = problem_base + problem index) */
   int32_t threads;        /* threads per particle block (32..256, multiple of 32); 0: default
                              (on TSMC_MIXED 256 for TSMC_SINUSOID, 96 for TSMC_PULSE; else
                              128) */
@@ -92,7 +92,15 @@ typedef struct {
                              time-domain one with sigma^2 = S / (2 dt) (Parseval; DC and
                              Nyquist bins aside).  No tsmc_assimilate for two channels. */
   double response[4];     /* channels = 2: (r_A, delta_A, r_E, delta_E), r_c > 0 */
+  int32_t problem_base;   /* >= 0: Philox key word 1 of problem b is problem_base + b.  A
+                             process that owns problems [a, a + n) of a larger set of
+                             independent problems sets it to a and draws exactly the random
+                             numbers a context over the whole set draws for them (sharding
+                             across GPUs needs no exchange); 0 for a single context */
 } tsmc_config;
+
+/* Opaque context: created by tsmc_create, released by tsmc_destroy. */
+typedef struct tsmc_ctx tsmc_ctx;
 
 /* Workspace size for a configuration and per-problem sample capacities
  * n_capacity_host[n_problems] (the largest N each problem will hold, including
@@ -107,30 +115,30 @@ tsmc_status tsmc_workspace_bytes(const tsmc_config* cfg, const int64_t* n_capaci
  * (NULL: legacy default stream).  The context keeps pointers into the workspace,
  * which must outlive it. */
 tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* n_capacity_host,
-                        void* workspace_dev, size_t bytes, void* cuda_stream, void** ctx_out);
-tsmc_status tsmc_destroy(void* ctx);
-const char* tsmc_last_error(const void* ctx);
+                        void* workspace_dev, size_t bytes, void* cuda_stream, tsmc_ctx** ctx_out);
+tsmc_status tsmc_destroy(tsmc_ctx* ctx);
+const char* tsmc_last_error(const tsmc_ctx* ctx);
 
 /* Data of one problem: samples d_n (host FP64, n <= capacity) on the grid
  * t_n = t_origin + n*dt with white noise sigma; per-parameter prior bounds
  * lo/hi (theta = lo + (hi-lo) s(z), or log-uniform where bit d of logmask is
  * set).  All samples count as new (n1 = 0).  Copies to the device. */
-tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, int64_t n,
+tsmc_status tsmc_set_problem(tsmc_ctx* ctx, int32_t problem, const double* d_host, int64_t n,
                              double t_origin, double dt, double sigma, const double* lo_host,
                              const double* hi_host, uint32_t logmask);
 
 /* LINAMP only: fixed (t0, w) per component, host [kmax][2]. */
-tsmc_status tsmc_set_fixed_components(void* ctx, const double* tw_host);
+tsmc_status tsmc_set_fixed_components(tsmc_ctx* ctx, const double* tw_host);
 
 /* Prior start (Sec. 4 step 1): K ~ U{kmin..kmax}, z ~ logistic (theta from its prior);
  * beta = 0, log Z = 0, step size eps_0 = 0.5 (kmax D)^(-1/4), unit metric. */
-tsmc_status tsmc_init_population(void* ctx);
+tsmc_status tsmc_init_population(tsmc_ctx* ctx);
 
 /* Posterior start / resume: population from device arrays, beta and log Z per problem. */
-tsmc_status tsmc_set_population(void* ctx, const double* z_dev, const int32_t* K_dev,
+tsmc_status tsmc_set_population(tsmc_ctx* ctx, const double* z_dev, const int32_t* K_dev,
                                 const double* beta_host, const double* logz_host);
 /* Copies the population out (any output may be NULL). */
-tsmc_status tsmc_get_population(void* ctx, double* z_dev, int32_t* K_dev, double* ll_old_dev,
+tsmc_status tsmc_get_population(tsmc_ctx* ctx, double* z_dev, int32_t* K_dev, double* ll_old_dev,
                                 double* ll_new_dev);
 
 /* Batched logL + adjoint gradient (hot path) over caller arrays for all
@@ -143,7 +151,7 @@ tsmc_status tsmc_get_population(void* ctx, double* z_dev, int32_t* K_dev, double
  *            sum_n c_n (dh/dz_d)^2/sigma^2 + prior curvature, [P][D]
  * beta_dev[n_problems] (NULL: the context's current beta).  Any output may be NULL
  * except ll_new_dev; grad and fisher cost a second pass over the samples. */
-tsmc_status tsmc_eval_logl_grad(void* ctx, const double* z_dev, const int32_t* K_dev,
+tsmc_status tsmc_eval_logl_grad(tsmc_ctx* ctx, const double* z_dev, const int32_t* K_dev,
                                 const double* beta_dev, double* ll_old_dev, double* ll_new_dev,
                                 double* logp_dev, double* grad_dev, double* fisher_dev);
 
@@ -154,18 +162,18 @@ tsmc_status tsmc_eval_logl_grad(void* ctx, const double* z_dev, const int32_t* K
  * -(r.h + h.h/2)/sigma^2 (death) with per-sample temperatures.  Random numbers
  * use (stage, round).  outcome_dev[P_total] (nullable): 0 no move, 1/2 birth/death
  * accepted, -1/-2 rejected. */
-tsmc_status tsmc_rj_move(void* ctx, int32_t stage, int32_t round, int32_t* outcome_dev);
+tsmc_status tsmc_rj_move(tsmc_ctx* ctx, int32_t stage, int32_t round, int32_t* outcome_dev);
 
 /* One NUTS transition per particle (Sec. 3.2) with the context's step size and
  * diagonal metric.  acc_dev (mean min(1, e^{H0-H}) over leaves), nleaf_dev,
  * flags_dev (bit0 divergence, bits 8-15 depth) are nullable [P_total] outputs. */
-tsmc_status tsmc_nuts_move(void* ctx, int32_t stage, int32_t round, double* acc_dev,
+tsmc_status tsmc_nuts_move(tsmc_ctx* ctx, int32_t stage, int32_t round, double* acc_dev,
                            int32_t* nleaf_dev, int32_t* flags_dev);
 
 /* Step size and inverse diagonal metric per problem: eps_host[n_problems],
  * minv_host[n_problems][D]. */
-tsmc_status tsmc_set_kernel_params(void* ctx, const double* eps_host, const double* minv_host);
-tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_host, double* minv_host);
+tsmc_status tsmc_set_kernel_params(tsmc_ctx* ctx, const double* eps_host, const double* minv_host);
+tsmc_status tsmc_get_kernel_params(tsmc_ctx* ctx, double* eps_host, double* minv_host);
 
 /* Population birth proposal (Sec. 6: the particles of each SMC stage approximate its
  * tempered distribution, so that distribution can propose births).  In z coordinates
@@ -179,30 +187,30 @@ tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_host, double* minv_hos
  * builds it now from the context population with the given stage number in the random
  * stream (stream-ordered; EINVAL for LINAMP or stage < 0).  Until a build, every problem's
  * proposal is the prior. */
-tsmc_status tsmc_build_birth_proposal(void* ctx, int32_t stage);
+tsmc_status tsmc_build_birth_proposal(tsmc_ctx* ctx, int32_t stage);
 
 /* The proposal of one problem into host out[n]: out[0] = m (0: none built or no
  * components), out[1..4] = h, out[5 ..] = centres [256][D] row-major.  n >= 5 + 256 D,
  * else EINVAL.  Synchronises the context stream. */
-tsmc_status tsmc_get_birth_proposal(void* ctx, int32_t problem, double* out_host, int64_t n);
+tsmc_status tsmc_get_birth_proposal(tsmc_ctx* ctx, int32_t problem, double* out_host, int64_t n);
 
 /* Metric from the population (Sec. 3.2, mass matrix = Hessian of -log target):
  * minv_d = 1 / max(1e-8, mean over particles and active components of the
  * Gauss-Newton diagonal at the current beta; particles with a non-finite diagonal
  * are left out). */
-tsmc_status tsmc_update_metric(void* ctx);
+tsmc_status tsmc_update_metric(tsmc_ctx* ctx);
 
 /* Choose beta by ESS bisection, reweight (evidence increment) and resample
  * systematically (Sec. 2 steps 1-2).  Host outputs (nullable) [n_problems]; with
  * all three NULL the call does not synchronise. */
-tsmc_status tsmc_temper_reweight_resample(void* ctx, int32_t stage, double* beta_host,
+tsmc_status tsmc_temper_reweight_resample(tsmc_ctx* ctx, int32_t stage, double* beta_host,
                                           double* logz_host, double* ess_host);
 /* Current beta, log Z and last ESS per problem (host [n_problems], nullable);
  * synchronises the stream. */
-tsmc_status tsmc_get_state(void* ctx, double* beta_host, double* logz_host, double* ess_host);
+tsmc_status tsmc_get_state(tsmc_ctx* ctx, double* beta_host, double* logz_host, double* ess_host);
 
 /* Ancestors of the last resampling, [P_total] local indices (test access). */
-tsmc_status tsmc_get_ancestors(void* ctx, int32_t* anc_dev);
+tsmc_status tsmc_get_ancestors(tsmc_ctx* ctx, int32_t* anc_dev);
 
 /* One whole stage: temper/reweight/resample, metric, n_mut mutation rounds,
  * step-size update eps <- eps exp(mean_acc - 0.8) clamped to [1e-4, 2].
@@ -210,18 +218,21 @@ tsmc_status tsmc_get_ancestors(void* ctx, int32_t* anc_dev);
  * (nullable) [n_problems]; with all three NULL the call does not synchronise
  * (stages can be queued back to back).  Uses a CUDA graph for the mutation rounds
  * when use_graph != 0 and the stream is not the legacy default stream. */
-tsmc_status tsmc_run_stage(void* ctx, int32_t stage, int32_t use_graph, double* beta_host,
+tsmc_status tsmc_run_stage(tsmc_ctx* ctx, int32_t stage, int32_t use_graph, double* beta_host,
                            double* logz_host, double* ess_host);
 
 /* Data assimilation (Eq. reuse_bridge, Sec. 5.1-5.2 posterior start): append
  * n_new samples to a problem, mark them new (n1 = old n), recompute each
  * particle's logL on the new samples and restart that problem's beta at 0.
- * The evidence accumulator restarts at 0 (it then estimates log Z(d2)/Z(d1)). */
-tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new_host, int64_t n_new);
+ * The evidence accumulator restarts at 0 (it then estimates log Z(d2)/Z(d1)).
+ * The bridge starts from the posterior of the samples held so far: a problem whose
+ * beta is below 1 is refused with TSMC_ESTATE (nothing changes).  Other problems keep
+ * their state.  Synchronises the stream. */
+tsmc_status tsmc_assimilate(tsmc_ctx* ctx, int32_t problem, const double* d_new_host, int64_t n_new);
 
 /* Philox4x64-10 (the library's random stream) on the device: out_dev[4*i..4*i+3]
  * = Philox(ctr_dev[4*i..4*i+3], {key0, key1}) for i < n. */
-tsmc_status tsmc_philox(void* ctx, const uint64_t* ctr_dev, uint64_t key0, uint64_t key1,
+tsmc_status tsmc_philox(tsmc_ctx* ctx, const uint64_t* ctr_dev, uint64_t key0, uint64_t key1,
                         int64_t n, uint64_t* out_dev);
 
 /* Statistics (no counterpart in the paper's method; measurement support):
@@ -231,7 +242,7 @@ tsmc_status tsmc_philox(void* ctx, const uint64_t* ctr_dev, uint64_t key0, uint6
  * evaluations counting only the component*samples actually computed (less than
  * [0], [1] when pulse_window skips the far tails).  launches_host = kernels launched.
  * reset != 0 zeroes both after reading.  Synchronises the stream. */
-tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_host,
+tsmc_status tsmc_counters(tsmc_ctx* ctx, uint64_t* cs_evals_host, int64_t* launches_host,
                           int32_t reset);
 
 /* Per-kernel-class event timing of eager launches (graphs are not used while it is
@@ -240,8 +251,8 @@ tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_
  * between events recorded on the context stream around each launch) and
  * synchronises the stream; reset != 0 forgets the records.  enable > 1 also
  * creates that many events up front (two per recorded launch). */
-tsmc_status tsmc_profile(void* ctx, int32_t enable);
-tsmc_status tsmc_profile_read(void* ctx, int64_t* launches_host, double* ms_host, int32_t reset);
+tsmc_status tsmc_profile(tsmc_ctx* ctx, int32_t enable);
+tsmc_status tsmc_profile_read(tsmc_ctx* ctx, int64_t* launches_host, double* ms_host, int32_t reset);
 
 /* Systematic resampling without any device allocation and without a context.
  *
@@ -275,7 +286,7 @@ tsmc_status tsmc_resample_systematic_static(const double* logw_dev, int32_t n_pr
                                             int32_t* ancestors_dev, void* cuda_stream);
 
 /* Waits for the stream; returns TSMC_ECUDA with a message on an asynchronous error. */
-tsmc_status tsmc_sync(void* ctx);
+tsmc_status tsmc_sync(tsmc_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -13,9 +13,8 @@
 
 using namespace tsmc;
 
-namespace {
-
-struct Ctx {
+// the context behind the opaque tsmc_ctx handle
+struct tsmc_ctx {
   tsmc_config cfg{};
   int D = 0, kd = 0, T = 0, R = 32;
   int64_t Ptot = 0;
@@ -59,6 +58,10 @@ struct Ctx {
   std::vector<cudaEvent_t> pool;
   std::string err;
 };
+
+namespace {
+
+using Ctx = tsmc_ctx;
 
 enum KClass { KC_EVAL = 0, KC_RJ = 1, KC_NUTS = 2, KC_TEMPER = 3, KC_RESAMPLE = 4, KC_GATHER = 5,
               KC_METRIC = 6, KC_OTHER = 7, KC_N = 8 };
@@ -111,6 +114,8 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->birth_proposal == 1 && !(cfg->birth_prior_weight > 0.0 && cfg->birth_prior_weight <= 1.0))
     return TSMC_EINVAL;
   if (cfg->channels < 0 || cfg->channels > 2) return TSMC_EINVAL;
+  if (cfg->problem_base < 0 || (int64_t)cfg->problem_base + cfg->n_problems > INT32_MAX)
+    return TSMC_EINVAL;
   if (cfg->channels == 2) {
     if (cfg->model != TSMC_SINUSOID) return TSMC_EINVAL;
     for (int q = 0; q < 4; ++q)
@@ -185,6 +190,7 @@ KParams kparams(Ctx* c) {
   kp.pa.amp_sd = c->cfg.amp_sd;
   kp.pa.window = (c->cfg.precision == TSMC_MIXED && c->cfg.pulse_window) ? 1 : 0;
   kp.seed = c->cfg.seed;
+  kp.prob_base = c->cfg.problem_base;
   kp.tw = c->tw;
   kp.z = c->z;
   kp.K = c->K;
@@ -375,11 +381,20 @@ tsmc_status require_ready(Ctx* c) {
   return TSMC_OK;
 }
 
+// every descriptor (resets the device-side done flags to the host copies)
 tsmc_status upload_probs(Ctx* c) {
   return cuda_check(c, cudaMemcpyAsync(c->probs, c->probs_host.data(),
                                        sizeof(ProbDev) * c->probs_host.size(),
                                        cudaMemcpyHostToDevice, c->stream),
                     "upload problem descriptors");
+}
+
+// one descriptor: the other problems keep their device state (k_temper sets done on the
+// device when a problem reaches beta = 1, and the host copies do not follow it)
+tsmc_status upload_prob(Ctx* c, int problem) {
+  return cuda_check(c, cudaMemcpyAsync(c->probs + problem, &c->probs_host[problem],
+                                       sizeof(ProbDev), cudaMemcpyHostToDevice, c->stream),
+                    "upload problem descriptor");
 }
 
 tsmc_status sync_stream(Ctx* c) {
@@ -443,7 +458,8 @@ tsmc_status temper_resample(Ctx* c, int stage) {
     TRY(last_launch(c, "k_temper"));
   }
   pre(c, KC_RESAMPLE);
-  k_resample<<<np, tt, 0, c->stream>>>(c->logw, c->cw, c->anc, c->probs, c->cfg.seed, stage, P);
+  k_resample<<<np, tt, 0, c->stream>>>(c->logw, c->cw, c->anc, c->probs, c->cfg.seed, stage, P,
+                                       c->cfg.problem_base);
   TRY(last_launch(c, "k_resample"));
   const int64_t work = c->Ptot * (c->kd + 1);
   const int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 16);
@@ -500,7 +516,7 @@ tsmc_status tsmc_workspace_bytes(const tsmc_config* cfg, const int64_t* cap, siz
 }
 
 tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, size_t bytes,
-                        void* stream, void** out) {
+                        void* stream, tsmc_ctx** out) {
   if (!out) return fail(nullptr, TSMC_EINVAL, "null output");
   size_t need = 0;
   TRY(tsmc_workspace_bytes(cfg, cap, &need));
@@ -586,8 +602,8 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   return TSMC_OK;
 }
 
-tsmc_status tsmc_destroy(void* ctx) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_destroy(tsmc_ctx* ctx) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (const Ctx::Rec& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -596,15 +612,15 @@ tsmc_status tsmc_destroy(void* ctx) {
   return TSMC_OK;
 }
 
-const char* tsmc_last_error(const void* ctx) {
-  const Ctx* c = static_cast<const Ctx*>(ctx);
+const char* tsmc_last_error(const tsmc_ctx* ctx) {
+  const Ctx* c = ctx;
   return c ? c->err.c_str() : g_err.c_str();
 }
 
-tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, int64_t n,
+tsmc_status tsmc_set_problem(tsmc_ctx* ctx, int32_t problem, const double* d_host, int64_t n,
                              double t_origin, double dt, double sigma, const double* lo,
                              const double* hi, uint32_t logmask) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (problem < 0 || problem >= c->cfg.n_problems) return fail(c, TSMC_EINVAL, "problem index out of range");
   if (!d_host || n <= 0 || n > c->cap[problem]) return fail(c, TSMC_EINVAL, "bad sample count");
@@ -650,13 +666,13 @@ tsmc_status tsmc_set_problem(void* ctx, int32_t problem, const double* d_host, i
   k_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, c->stream>>>(
       pd.d64, const_cast<float*>(pd.d32), n);
   TRY(last_launch(c, "k_to_f32"));
-  TRY(upload_probs(c));
+  TRY(upload_prob(c, problem));
   c->has_data[problem] = 1;
   return sync_stream(c);
 }
 
-tsmc_status tsmc_set_fixed_components(void* ctx, const double* tw_host) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_set_fixed_components(tsmc_ctx* ctx, const double* tw_host) {
+  Ctx* c = ctx;
   if (!c || !tw_host) return TSMC_EINVAL;
   if (!all_finite(tw_host, 2 * c->cfg.kmax)) return fail(c, TSMC_ENONFINITE, "non-finite components");
   for (int k = 0; k < c->cfg.kmax; ++k)
@@ -686,8 +702,8 @@ static tsmc_status reset_run_state(Ctx* c, const double* beta_h, const double* l
   return sync_stream(c);
 }
 
-tsmc_status tsmc_init_population(void* ctx) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_init_population(tsmc_ctx* ctx) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   TRY(require_ready(c));
   TRY(reset_run_state(c, nullptr, nullptr));
@@ -700,9 +716,9 @@ tsmc_status tsmc_init_population(void* ctx) {
   return sync_stream(c);
 }
 
-tsmc_status tsmc_set_population(void* ctx, const double* z_dev, const int32_t* K_dev,
+tsmc_status tsmc_set_population(tsmc_ctx* ctx, const double* z_dev, const int32_t* K_dev,
                                 const double* beta_h, const double* logz_h) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c || !z_dev || !K_dev) return TSMC_EINVAL;
   TRY(require_ready(c));
   if (beta_h)
@@ -721,9 +737,9 @@ tsmc_status tsmc_set_population(void* ctx, const double* z_dev, const int32_t* K
   return sync_stream(c);
 }
 
-tsmc_status tsmc_get_population(void* ctx, double* z_dev, int32_t* K_dev, double* llo_dev,
+tsmc_status tsmc_get_population(tsmc_ctx* ctx, double* z_dev, int32_t* K_dev, double* llo_dev,
                                 double* lln_dev) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (z_dev) TRY_CUDA(c, cudaMemcpyAsync(z_dev, c->z, sizeof(double) * c->Ptot * c->kd, cudaMemcpyDeviceToDevice, c->stream));
@@ -733,10 +749,10 @@ tsmc_status tsmc_get_population(void* ctx, double* z_dev, int32_t* K_dev, double
   return TSMC_OK;
 }
 
-tsmc_status tsmc_eval_logl_grad(void* ctx, const double* z_dev, const int32_t* K_dev,
+tsmc_status tsmc_eval_logl_grad(tsmc_ctx* ctx, const double* z_dev, const int32_t* K_dev,
                                 const double* beta_dev, double* llo_dev, double* lln_dev,
                                 double* logp_dev, double* grad_dev, double* fis_dev) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!z_dev || !K_dev || !lln_dev) return fail(c, TSMC_EINVAL, "null argument");
   TRY(require_ready(c));
@@ -744,8 +760,8 @@ tsmc_status tsmc_eval_logl_grad(void* ctx, const double* z_dev, const int32_t* K
   return eval_launch(c, io, grad_dev != nullptr, fis_dev != nullptr);
 }
 
-tsmc_status tsmc_rj_move(void* ctx, int32_t stage, int32_t round, int32_t* outcome_dev) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_rj_move(tsmc_ctx* ctx, int32_t stage, int32_t round, int32_t* outcome_dev) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (stage < 0 || round < 0 || round > 0x0FFFFFFF) return fail(c, TSMC_EINVAL, "bad stage/round");
@@ -754,9 +770,9 @@ tsmc_status tsmc_rj_move(void* ctx, int32_t stage, int32_t round, int32_t* outco
   return rj_launch(c, round, outcome_dev);
 }
 
-tsmc_status tsmc_nuts_move(void* ctx, int32_t stage, int32_t round, double* acc_dev,
+tsmc_status tsmc_nuts_move(tsmc_ctx* ctx, int32_t stage, int32_t round, double* acc_dev,
                            int32_t* nleaf_dev, int32_t* flags_dev) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (stage < 0 || round < 0 || round > 0x0FFFFFFF) return fail(c, TSMC_EINVAL, "bad stage/round");
@@ -764,8 +780,8 @@ tsmc_status tsmc_nuts_move(void* ctx, int32_t stage, int32_t round, double* acc_
   return nuts_launch(c, round, NutsOut{acc_dev, nleaf_dev, flags_dev});
 }
 
-tsmc_status tsmc_set_kernel_params(void* ctx, const double* eps_h, const double* minv_h) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_set_kernel_params(tsmc_ctx* ctx, const double* eps_h, const double* minv_h) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   const int np = c->cfg.n_problems;
   if (eps_h) {
@@ -786,16 +802,16 @@ tsmc_status tsmc_set_kernel_params(void* ctx, const double* eps_h, const double*
   return sync_stream(c);
 }
 
-tsmc_status tsmc_build_birth_proposal(void* ctx, int32_t stage) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_build_birth_proposal(tsmc_ctx* ctx, int32_t stage) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (c->cfg.model == TSMC_PULSE_LINAMP || stage < 0)
     return fail(c, TSMC_EINVAL, "no birth proposal for this model or stage");
   return kde_launch(c, stage);
 }
 
-tsmc_status tsmc_get_birth_proposal(void* ctx, int32_t problem, double* out_h, int64_t n) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_get_birth_proposal(tsmc_ctx* ctx, int32_t problem, double* out_h, int64_t n) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!out_h || problem < 0 || problem >= c->cfg.n_problems || n < 5 + (int64_t)kKdeM * c->D)
     return fail(c, TSMC_EINVAL, "bad problem or output size");
@@ -809,8 +825,8 @@ tsmc_status tsmc_get_birth_proposal(void* ctx, int32_t problem, double* out_h, i
   return TSMC_OK;
 }
 
-tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_h, double* minv_h) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_get_kernel_params(tsmc_ctx* ctx, double* eps_h, double* minv_h) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   const int np = c->cfg.n_problems;
   std::vector<double> m(4 * np);
@@ -823,8 +839,8 @@ tsmc_status tsmc_get_kernel_params(void* ctx, double* eps_h, double* minv_h) {
   return TSMC_OK;
 }
 
-tsmc_status tsmc_update_metric(void* ctx) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_update_metric(tsmc_ctx* ctx) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   EvalIO io{c->z, c->K, c->beta, c->llo, c->lln, nullptr, nullptr, c->fis};
@@ -834,9 +850,9 @@ tsmc_status tsmc_update_metric(void* ctx) {
   return last_launch(c, "k_metric");
 }
 
-tsmc_status tsmc_temper_reweight_resample(void* ctx, int32_t stage, double* beta_h,
+tsmc_status tsmc_temper_reweight_resample(tsmc_ctx* ctx, int32_t stage, double* beta_h,
                                           double* logz_h, double* ess_h) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (stage < 0) return fail(c, TSMC_EINVAL, "bad stage");
@@ -844,23 +860,23 @@ tsmc_status tsmc_temper_reweight_resample(void* ctx, int32_t stage, double* beta
   return read_problem_scalars(c, beta_h, logz_h, ess_h);
 }
 
-tsmc_status tsmc_get_state(void* ctx, double* beta_h, double* logz_h, double* ess_h) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_get_state(tsmc_ctx* ctx, double* beta_h, double* logz_h, double* ess_h) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   TRY(read_problem_scalars(c, beta_h, logz_h, ess_h));
   return sync_stream(c);
 }
 
-tsmc_status tsmc_get_ancestors(void* ctx, int32_t* anc_dev) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_get_ancestors(tsmc_ctx* ctx, int32_t* anc_dev) {
+  Ctx* c = ctx;
   if (!c || !anc_dev) return TSMC_EINVAL;
   TRY_CUDA(c, cudaMemcpyAsync(anc_dev, c->anc, sizeof(int32_t) * c->Ptot, cudaMemcpyDeviceToDevice, c->stream));
   return TSMC_OK;
 }
 
-tsmc_status tsmc_run_stage(void* ctx, int32_t stage, int32_t use_graph, double* beta_h,
+tsmc_status tsmc_run_stage(tsmc_ctx* ctx, int32_t stage, int32_t use_graph, double* beta_h,
                            double* logz_h, double* ess_h) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (stage < 0) return fail(c, TSMC_EINVAL, "bad stage");
@@ -890,8 +906,8 @@ tsmc_status tsmc_run_stage(void* ctx, int32_t stage, int32_t use_graph, double* 
   return read_problem_scalars(c, beta_h, logz_h, ess_h);
 }
 
-tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new, int64_t n_new) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_assimilate(tsmc_ctx* ctx, int32_t problem, const double* d_new, int64_t n_new) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (problem < 0 || problem >= c->cfg.n_problems) return fail(c, TSMC_EINVAL, "problem index out of range");
   if (!c->pop_ready || !c->has_data[problem]) return fail(c, TSMC_ESTATE, "no population");
@@ -899,6 +915,15 @@ tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new, int
   if (!d_new || n_new <= 0 || pd.n + n_new > pd.cap) return fail(c, TSMC_EINVAL, "bad sample count");
   if (pd.nch == 2) return fail(c, TSMC_EINVAL, "two-channel problems take no appended samples");
   if (!all_finite(d_new, n_new)) return fail(c, TSMC_ENONFINITE, "non-finite data");
+  // the reuse bridge (Eq. reuse_bridge) starts from the posterior of the samples held so
+  // far: particles still tempered (beta < 1) would enter it with unit weight and no
+  // importance correction
+  double beta_now = 0.0;
+  TRY_CUDA(c, cudaMemcpyAsync(&beta_now, c->beta + problem, sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+  TRY(sync_stream(c));
+  if (!(beta_now >= 1.0))
+    return fail(c, TSMC_ESTATE, "assimilate needs the posterior of the data held so far (beta = 1)");
   TRY_CUDA(c, cudaMemcpyAsync(const_cast<double*>(pd.d64) + pd.n, d_new, sizeof(double) * n_new,
                               cudaMemcpyHostToDevice, c->stream));
   pre(c, KC_OTHER);
@@ -908,7 +933,7 @@ tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new, int
   pd.n1 = pd.n;
   pd.n += n_new;
   pd.done = 0;
-  TRY(upload_probs(c));
+  TRY(upload_prob(c, problem));
   const double zero = 0.0;
   TRY_CUDA(c, cudaMemcpyAsync(c->beta + problem, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   TRY_CUDA(c, cudaMemcpyAsync(c->logz + problem, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -916,9 +941,9 @@ tsmc_status tsmc_assimilate(void* ctx, int32_t problem, const double* d_new, int
   return sync_stream(c);
 }
 
-tsmc_status tsmc_philox(void* ctx, const uint64_t* ctr_dev, uint64_t key0, uint64_t key1,
+tsmc_status tsmc_philox(tsmc_ctx* ctx, const uint64_t* ctr_dev, uint64_t key0, uint64_t key1,
                         int64_t n, uint64_t* out_dev) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c || !ctr_dev || !out_dev || n < 0) return TSMC_EINVAL;
   if (n == 0) return TSMC_OK;
   pre(c, KC_OTHER);
@@ -926,9 +951,9 @@ tsmc_status tsmc_philox(void* ctx, const uint64_t* ctr_dev, uint64_t key0, uint6
   return last_launch(c, "k_philox");
 }
 
-tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_host,
+tsmc_status tsmc_counters(tsmc_ctx* ctx, uint64_t* cs_evals_host, int64_t* launches_host,
                           int32_t reset) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   unsigned long long v[4] = {0, 0, 0, 0};
   TRY_CUDA(c, cudaMemcpyAsync(v, c->cs_count, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
@@ -944,8 +969,8 @@ tsmc_status tsmc_counters(void* ctx, uint64_t* cs_evals_host, int64_t* launches_
   return TSMC_OK;
 }
 
-tsmc_status tsmc_profile(void* ctx, int32_t enable) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_profile(tsmc_ctx* ctx, int32_t enable) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   c->profiling = enable != 0;
   // create the events up front: no driver object creation inside a timed region
@@ -957,8 +982,8 @@ tsmc_status tsmc_profile(void* ctx, int32_t enable) {
   return TSMC_OK;
 }
 
-tsmc_status tsmc_profile_read(void* ctx, int64_t* launches_host, double* ms_host, int32_t reset) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_profile_read(tsmc_ctx* ctx, int64_t* launches_host, double* ms_host, int32_t reset) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   TRY(sync_stream(c));
   std::vector<int64_t> n(KC_N, 0);
@@ -1042,14 +1067,14 @@ tsmc_status tsmc_resample_systematic_static(const double* logw_dev, int32_t n_pr
   TRY(static_scratch(&prefix, &probs));
   const int tt = particles >= 1024 ? 1024 : ((particles + 31) / 32) * 32;
   k_resample<<<n_problems, tt, 0, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(
-      logw_dev, prefix, ancestors_dev, probs, seed, stage, particles);
+      logw_dev, prefix, ancestors_dev, probs, seed, stage, particles, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, TSMC_ECUDA, std::string("k_resample: ") + cudaGetErrorString(e));
   return TSMC_OK;
 }
 
-tsmc_status tsmc_sync(void* ctx) {
-  Ctx* c = static_cast<Ctx*>(ctx);
+tsmc_status tsmc_sync(tsmc_ctx* ctx) {
+  Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   return sync_stream(c);
 }

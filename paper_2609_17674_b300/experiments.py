@@ -56,6 +56,9 @@ def segment_experiment(wl: Workload, seg_seconds: float = 20.0, precision: int =
         if i == 0:
             out, wall = run(ctx)
         else:
+            if not posterior[-1]["reached"]:
+                raise RuntimeError(f"segment {i - 1} stopped at beta < 1 after {max_stages} "
+                                   "stages: its particles are not a posterior to start from")
             ctx.assimilate(0, pr.d[bounds[i - 1]:nb])
             out, wall = run(ctx, stage0=1000 * i, init_prior=False)
         logz += float(out["logz"][-1][0])

@@ -29,11 +29,11 @@ def context_with_population(wl, precision, z, K, beta, n_use=None, n1=0, threads
     t = torch()
     zt = dev_tensor(z, t.float64)
     Kt = dev_tensor(K, t.int32)
-    ctx.set_population(zt, Kt, beta=[beta] * len(wl.problems))
     if n1 > 0:
+        # assimilation starts from a posterior (beta = 1) of the first n1 samples
+        ctx.set_population(zt, Kt, beta=[1.0] * len(wl.problems))
         ctx.assimilate(0, pr.d[n1:n_use])
-        bt = dev_tensor(np.full(len(wl.problems), beta), t.float64)
-        ctx.set_population(zt, Kt, beta=[beta] * len(wl.problems))
+    ctx.set_population(zt, Kt, beta=[beta] * len(wl.problems))
     return ctx, zt, Kt
 
 

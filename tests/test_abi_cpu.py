@@ -27,6 +27,25 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(capi.SIGNATURES)
 
 
+def test_header_is_plain_c_with_a_typed_context(tmp_path):
+    """The header compiles as C11; the context handle is an opaque struct pointer, so
+    passing any other pointer where a context is expected is a compile error."""
+    import subprocess
+
+    inc = os.path.join(ROOT, "include")
+    good = tmp_path / "good.c"
+    good.write_text('#include "tsmc.h"\n'
+                    'int f(tsmc_ctx* c) { return (int)tsmc_sync(c) + (int)tsmc_destroy(c); }\n')
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", inc, "-c", str(good),
+                           "-o", str(tmp_path / "good.o")])
+    bad = tmp_path / "bad.c"
+    bad.write_text('#include "tsmc.h"\n'
+                   'int f(tsmc_config* c) { return (int)tsmc_sync(c); }\n')
+    r = subprocess.run(["gcc", "-std=c11", "-Werror=incompatible-pointer-types", "-I", inc,
+                        "-c", str(bad), "-o", str(tmp_path / "bad.o")], capture_output=True)
+    assert r.returncode != 0
+
+
 def test_workspace_bytes_and_config_validation():
     L = capi.lib()
     wl = synth.pulse_k20()

@@ -88,6 +88,28 @@ def test_assimilate_likelihood_of_new_samples():
         assert b[0] == 0.0 and lz[0] == 0.0
 
 
+def test_assimilate_refuses_a_population_still_tempered():
+    """The reuse bridge starts from the posterior of the data held so far: at beta < 1 the
+    call is refused (TSMC_ESTATE) and changes nothing; at beta = 1 it goes ahead."""
+    t = torch()
+    wl = synth.assimilation_pulse_k14(P=64, n_full=1 << 14)
+    pr = wl.problems[0]
+    z, K = population(wl, 3, 64)
+    n1 = 1 << 12
+    ctx = sampler.open_context(wl, capi.FP64, n_use=n1, n_capacity=[pr.n])
+    zd, Kd = dev_tensor(z, t.float64), dev_tensor(K, t.int32)
+    ctx.set_population(zd, Kd, beta=[0.4])
+    _, _, lo0, ln0 = ctx.get_population()
+    with pytest.raises(capi.TsmcError, match="tsmc error -6"):
+        ctx.assimilate(0, pr.d[n1:1 << 13])
+    _, _, lo1, ln1 = ctx.get_population()
+    assert t.equal(lo0, lo1) and t.equal(ln0, ln1)
+    assert ctx.temper_state()[0][0] == 0.4
+    ctx.set_population(zd, Kd, beta=[1.0])
+    ctx.assimilate(0, pr.d[n1:1 << 13])
+    assert ctx.temper_state()[0][0] == 0.0
+
+
 def test_posterior_start_stage_matches_oracle_fp64():
     """First stage after assimilation: old samples untempered, new ones tempered by beta."""
     wl = synth.pulse_workload("assim", 2048, 3, 5, 128, 12, n_mut=2)
@@ -145,3 +167,30 @@ def test_posterior_start_consistent_with_prior_start():
     zt, zts = np.mean(two_z), np.std(two_z, ddof=1) / 2
     assert abs(zf - zt) <= 3 * math.hypot(zs, zts) + 0.5, (zf, zt)
     assert np.mean(st_post) < np.mean(st_full)
+
+
+def test_sharded_bands_reproduce_the_whole_set_fp64():
+    """Independent problems split into blocks, each block a context of its own with
+    problem_base = its first global index (what a rank runs under torchrun), give exactly
+    the results of one context over all of them: no exchange between blocks is needed."""
+    from paper_2609_17674_b300 import dist as tdist
+
+    t = torch()
+    full = synth.gb_bands(n_bands=5, P=48, log2n=(10, 11))
+    full.n_mut = 2
+
+    def run(wl):
+        ctx = sampler.open_context(wl, capi.FP64)
+        ctx.init_population()
+        for s in range(3):
+            ctx.run_stage(s, use_graph=False)
+        z, K, lo, ln = ctx.get_population()
+        b, lz, e = ctx.temper_state()
+        res = (z.cpu().numpy(), K.cpu().numpy(), ln.cpu().numpy(), b, lz)
+        ctx.close()
+        return res
+
+    whole = run(full)
+    parts = [run(tdist.shard_problems(full, 2, r)[0]) for r in range(2)]
+    for i in range(5):
+        assert np.array_equal(np.concatenate([p[i] for p in parts]), whole[i]), i
