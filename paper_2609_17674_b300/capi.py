@@ -69,6 +69,7 @@ class Config(C.Structure):
         ("pulse_window", C.c_int32), ("kmin", C.c_int32),
         ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
         ("channels", C.c_int32), ("response", C.c_double * 4),
+        ("problem_base", C.c_int32),
     ]
 
 
@@ -100,8 +101,31 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _check_device_array(name, t, dtype, n):
+    """t must be a contiguous CUDA tensor of dtype on the current device with >= n elements
+    (the C side cannot check the size of a device buffer)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, not the current device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+
+
 def resample_systematic_static(logw, n_problems, particles, seed, stage, ancestors, stream):
     """Allocation-free systematic resampling (static device scratch); see include/tsmc.h."""
+    import torch
+
+    n = int(n_problems) * int(particles)
+    if n_problems >= 1 and particles >= 1:   # sizes themselves are checked by the library
+        _check_device_array("logw", logw, torch.float64, n)
+        _check_device_array("ancestors", ancestors, torch.int32, n)
     L = lib()
     st = L.tsmc_resample_systematic_static(_ptr(logw), n_problems, particles, seed, stage,
                                            _ptr(ancestors), stream.cuda_stream)

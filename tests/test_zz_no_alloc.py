@@ -42,6 +42,7 @@ def test_static_resampling_matches_context_path_twice():
         ctx, logw, anc = _context_ancestors(wl, stage)
         logw_d = torch.as_tensor(logw, device="cuda")
         out = torch.full((logw.shape[0],), -1, dtype=torch.int32, device="cuda")
+        stream.wait_stream(torch.cuda.current_stream())   # the fill above runs on torch's stream
         capi.resample_systematic_static(logw_d, 2, wl.P, wl.seed, stage, out, stream)
         stream.synchronize()
         got = out.cpu().numpy()
@@ -61,3 +62,18 @@ def test_static_resampling_rejects_oversize():
         capi.resample_systematic_static(logw, 1, 65537, 1, 0, out, stream)
     with pytest.raises(capi.TsmcError, match="static limit of 256"):
         capi.resample_systematic_static(logw, 257, 2, 1, 0, out, stream)
+
+
+def test_static_resampling_binding_checks_buffers():
+    """The binding refuses buffers the kernel would overrun or misread (the C side cannot
+    check device buffer sizes): too short, wrong dtype, not contiguous, on the host."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    logw = torch.zeros(64, dtype=torch.float64, device="cuda")
+    out = torch.zeros(64, dtype=torch.int32, device="cuda")
+    for lw, o in ((logw[:63], out), (logw, out[:32]), (logw.float(), out),
+                  (logw, out.long()), (torch.zeros(128, dtype=torch.float64, device="cuda")[::2],
+                                       out), (logw.cpu(), out)):
+        with pytest.raises(ValueError):
+            capi.resample_systematic_static(lw, 2, 32, 1, 0, o, stream)
