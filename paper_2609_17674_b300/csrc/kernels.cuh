@@ -18,6 +18,7 @@ struct KParams {
   const double* kde;         // [n_problems][kKdeStride] population birth proposals
   PriorArgs pa;
   uint64_t seed;
+  int32_t prob_base;         // Philox key word 1 = prob_base + problem index
   const double* tw;          // LINAMP fixed (t0, w), [kmax][2]
   double* z;                 // [Ptot][kmax][D]
   int32_t* K;                // [Ptot]
@@ -150,6 +151,7 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= Ptot) return;
   const int prob = (int)(gi / kp.P);
+  const int pkey = prob + kp.prob_base;
   const uint64_t li = (uint64_t)(gi % kp.P);
   const int kd = kp.kmax * kp.D;
   double* z = kp.z + gi * kd;
@@ -158,15 +160,15 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
     kp.K[gi] = kp.kmax;
     for (int j = 0; j < kp.kmax; ++j)
       z[j] = kp.pa.amp_mean +
-             kp.pa.amp_sd * draw_normal(kp.seed, prob, li, 0, 0, PU_INIT, 4 + (uint64_t)j);
+             kp.pa.amp_sd * draw_normal(kp.seed, pkey, li, 0, 0, PU_INIT, 4 + (uint64_t)j);
     return;
   }
-  Rand4 w = draw(kp.seed, prob, li, 0, 0, PU_INIT, 0);
+  Rand4 w = draw(kp.seed, pkey, li, 0, 0, PU_INIT, 0);
   int k = kp.kmin + (int)floor(__dmul_rn(u01(w.w[0]), (double)(kp.kmax - kp.kmin + 1)));
   if (k > kp.kmax) k = kp.kmax;
   kp.K[gi] = k;
   for (int j = 0; j < k * kp.D; ++j) {
-    if ((j & 3) == 0) w = draw(kp.seed, prob, li, 0, 0, PU_INIT, 1 + (uint64_t)(j >> 2));
+    if ((j & 3) == 0) w = draw(kp.seed, pkey, li, 0, 0, PU_INIT, 1 + (uint64_t)(j >> 2));
     const double u = u01(w.w[j & 3]);
     z[j] = log(u) - log1p(-u);
   }
@@ -243,6 +245,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   __shared__ double s_znew[4];
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
+  const int pkey = prob + kp.prob_base;
   const uint64_t li = (uint64_t)(gi % kp.P);
   __shared__ ProbDev s_pb;
   const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
@@ -252,11 +255,11 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
   const int tid = threadIdx.x;
   if (tid == 0) {
     int move = 0;
-    const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_RJ, 0);
+    const Rand4 w = draw(kp.seed, pkey, li, stage, round, PU_RJ, 0);
     bool birth;
     bool active = kp.model != PULSE_LINAMP;
     if (active && kp.schedule == 1) {
-      const Rand4 m = draw(kp.seed, prob, li, stage, round, PU_MOVETYPE, 0);
+      const Rand4 m = draw(kp.seed, pkey, li, stage, round, PU_MOVETYPE, 0);
       const double um = u01(m.w[0]);
       active = !(um < kp.p_nuts);
       birth = um < kp.p_nuts + kp.p_birth;
@@ -270,9 +273,9 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
       else move = birth ? 1 : 2;
     }
     if (move == 1) {
-      const Rand4 pw = draw(kp.seed, prob, li, stage, round, PU_RJPARAM, 0);
+      const Rand4 pw = draw(kp.seed, pkey, li, stage, round, PU_RJPARAM, 0);
       const double* kde = kp.kde + (int64_t)prob * kKdeStride;
-      const Rand4 mw = draw(kp.seed, prob, li, stage, round, PU_RJPARAM, 2);
+      const Rand4 mw = draw(kp.seed, pkey, li, stage, round, PU_RJPARAM, 2);
       const int m = kp.birth_proposal ? (int)kde[0] : 0;
       if (m > 0 && u01(mw.w[0]) >= kp.birth_eps) {
         // from the population mixture: a centre, then a normal step of width h
@@ -280,7 +283,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
         if (q >= m) q = m - 1;
         for (int d = 0; d < D; ++d)
           s_znew[d] = __dadd_rn(kde[8 + q * D + d],
-                                __dmul_rn(kde[1 + d], draw_normal(kp.seed, prob, li, stage, round,
+                                __dmul_rn(kde[1 + d], draw_normal(kp.seed, pkey, li, stage, round,
                                                                   PU_RJPARAM, 4 + (uint64_t)d)));
       } else {
         for (int d = 0; d < D; ++d) {
@@ -466,7 +469,7 @@ __global__ void k_kde_build(KParams kp, int32_t* kcum, double* kde_out, double f
   }
   const int64_t kd = (int64_t)kp.kmax * D;
   for (int i = tid; i < kKdeM; i += T) {
-    const Rand4 w = draw(kp.seed, prob, (uint64_t)i, stage, 0, PU_KDE, 0);
+    const Rand4 w = draw(kp.seed, prob + kp.prob_base, (uint64_t)i, stage, 0, PU_KDE, 0);
     int32_t q = (int32_t)floor(__dmul_rn(u01(w.w[0]), (double)total));
     if (q >= total) q = total - 1;
     int a = 0, b = P - 1;   // first particle whose inclusive count exceeds q
@@ -561,6 +564,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   __shared__ double s_uleaf;   // uniform of the next leaf's multinomial choice
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
+  const int pkey = prob + kp.prob_base;
   const uint64_t li = (uint64_t)(gi % kp.P);
   __shared__ ProbDev s_pb;
   const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
@@ -571,7 +575,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   const int n = K * D;
   bool run = n > 0;
   if (kp.schedule == 1) {
-    const Rand4 m = draw(kp.seed, prob, li, stage, round, PU_MOVETYPE, 0);
+    const Rand4 m = draw(kp.seed, pkey, li, stage, round, PU_MOVETYPE, 0);
     run = run && (u01(m.w[0]) < kp.p_nuts);
   }
   if (!run) {
@@ -624,7 +628,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       if (warp == 0) {
         int dir = 0;
         if (lane == 0) {
-          const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_DIRECTION, (uint64_t)depth);
+          const Rand4 w = draw(kp.seed, pkey, li, stage, round, PU_DIRECTION, (uint64_t)depth);
           dir = u01(w.w[0]) < 0.5 ? -1 : 1;
           s_ctl[5] = -INFINITY;
           s_flag[0] = 1;
@@ -651,7 +655,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         }
       }
       if (l > 0 && tid == blockDim.x - 1) {   // the leaf's uniform, off the control path
-        const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_LEAF,
+        const Rand4 w = draw(kp.seed, pkey, li, stage, round, PU_LEAF,
                              (uint64_t)((nsub - 1) + l));
         s_uleaf = u01(w.w[0]);
       }
@@ -669,7 +673,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       if (warp == 0) {
         for (int i = lane; i < n; i += 32) {
           const CT pm = sqrt((CT)1 / minv[i % D]) *
-                        momentum_normal<CT>(kp.seed, prob, li, stage, round, (uint64_t)i);
+                        momentum_normal<CT>(kp.seed, pkey, li, stage, round, (uint64_t)i);
           pL[i] = pm; pR[i] = pm; rho[i] = pm;
           zL[i] = zc[i]; zR[i] = zc[i];
           gL[i] = g1[i]; gR[i] = g1[i];
@@ -775,7 +779,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = g1[i]; }
       int take = 0;
       if (lane == 0) {
-        const Rand4 w = draw(kp.seed, prob, li, stage, round, PU_TOP, (uint64_t)depth);
+        const Rand4 w = draw(kp.seed, pkey, li, stage, round, PU_TOP, (uint64_t)depth);
         take = u01(w.w[0]) < (double)ct_exp((CT)(s_ctl[5] - s_ctl[1]));
         if (take) { s_ctl[3] = s_ctl[6]; s_ctl[4] = s_ctl[7]; }
         s_ctl[1] = lae<CT>(s_ctl[1], s_ctl[5]);
@@ -1000,7 +1004,8 @@ __global__ void __launch_bounds__(1024) k_temper_mixed(TemperIO io, int P, float
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_resample(const double* logw_all, double* cw_all,
                                                    int32_t* anc_all, const ProbDev* probs,
-                                                   uint64_t seed, int stage, int P) {
+                                                   uint64_t seed, int stage, int P,
+                                                   int prob_base) {
   __shared__ double red[128];
   __shared__ double s_carry[33];
   __shared__ double s_m;
@@ -1048,7 +1053,7 @@ __global__ void __launch_bounds__(1024) k_resample(const double* logw_all, doubl
   for (int i = b; i < e; ++i) C[i] += off;
   __syncthreads();
   const double total = C[P - 1];
-  const Rand4 w = draw(seed, prob, 0, stage, 0, PU_RESAMPLE, 0);
+  const Rand4 w = draw(seed, prob + prob_base, 0, stage, 0, PU_RESAMPLE, 0);
   const double U = u01(w.w[0]);
   for (int i = tid; i < P; i += T) {
     const double target = ((double)i + U) / (double)P * total;

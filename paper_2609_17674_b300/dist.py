@@ -1,9 +1,15 @@
-"""Multi-GPU bookkeeping for weak scaling (one process per GPU, no data-path collective).
+"""Multi-GPU bookkeeping (one process per GPU, no data-path collective).
 
-Independent problems are sharded across ranks; only the measurement is reduced:
-the elapsed time as the maximum over ranks and the evaluation counts as their sum.
+Independent problems (the batched bands) are sharded across ranks: each rank owns a
+contiguous block of them and runs its own context with problem_base set to the block's
+first index, so every problem draws the same random numbers as in a single context over
+the whole set and the union of the ranks' results is the single-GPU result.  Only the
+measurement is reduced: the elapsed time as the maximum over ranks and the evaluation
+counts as their sum.
 """
 from __future__ import annotations
+
+import dataclasses
 
 
 def shard(n_units: int, world: int, rank: int):
@@ -11,6 +17,18 @@ def shard(n_units: int, world: int, rank: int):
     base, extra = divmod(n_units, world)
     start = rank * base + min(rank, extra)
     return list(range(start, start + base + (1 if rank < extra else 0)))
+
+
+def shard_problems(wl, world: int, rank: int):
+    """(workload of the problems rank owns, their indices in wl).  The shard keeps the
+    problems' global indices as its Philox keys (problem_base)."""
+    idx = shard(len(wl.problems), world, rank)
+    if not idx:
+        return None, idx
+    sub = dataclasses.replace(wl, problems=[wl.problems[b] for b in idx],
+                              problem_base=wl.problem_base + idx[0],
+                              name=f"{wl.name}[{idx[0]}:{idx[-1] + 1}]")
+    return sub, idx
 
 
 def rank_seed(seed: int, rank: int) -> int:

@@ -24,7 +24,8 @@ def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
                        p_birth=wl.p_birth, p_death=wl.p_death, amp_mean=wl.amp_mean,
                        amp_sd=wl.amp_sd, seed=wl.seed, threads=threads,
                        samples_per_thread=samples_per_thread,
-                       pulse_window=pulse_window if precision == capi.MIXED else 0)
+                       pulse_window=pulse_window if precision == capi.MIXED else 0,
+                       problem_base=wl.problem_base)
 
 
 def open_context(wl: Workload, precision=capi.MIXED, n_use=None, n_capacity=None, threads=0,

@@ -73,6 +73,7 @@ class Workload:
     birth_prior_weight: float = 0.2   # prior weight of the population mixture
     channels: int = 1         # sinusoids: 2 = channels A and E, data [A samples, E samples]
     resp: tuple = (1.0, 0.0, 1.0, 0.0)   # (r_A, delta_A, r_E, delta_E)
+    problem_base: int = 0     # index of problems[0] in a larger set (a shard of it)
 
     @property
     def D(self) -> int:

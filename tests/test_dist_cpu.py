@@ -1,4 +1,5 @@
-"""The weak-scaling bookkeeping of the multi-rank benchmark, on CPU with gloo, 2 ranks."""
+"""Multi-rank bookkeeping on CPU with gloo, 2 ranks: the measurement reduction of the
+benchmark and the sharding of the batched bands across ranks."""
 import os
 
 import torch.multiprocessing as mp
@@ -42,3 +43,51 @@ def test_reduce_measurement_two_ranks_gloo():
     assert [o[1] for o in out] == [15.0, 15.0]          # max over ranks
     assert [o[2] for o in out] == [3e12, 3e12]          # sum over ranks
     assert out[0][3] != out[1][3]                        # independent problems per rank
+
+
+def _band_worker(rank, world, port, q):
+    import numpy as np
+    import torch.distributed as dist
+
+    from paper_2609_17674_b300 import synth
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    full = synth.gb_bands(n_bands=7, P=16, log2n=(10, 11))
+    sub, idx = tdist.shard_problems(full, world, rank)
+    # the shard is the owned block of the full set, keyed by its global indices
+    assert sub.problem_base == idx[0]
+    for j, b in enumerate(idx):
+        assert np.array_equal(sub.problems[j].d, full.problems[b].d)
+        assert sub.bounds(j) == full.bounds(b)
+    owned = [None] * world
+    dist.all_gather_object(owned, idx)
+    cs = float(sum(full.problems[b].n for b in idx))
+    ms, cs_tot = tdist.reduce_measurement(3.0 + rank, cs)
+    q.put((rank, owned, ms, cs_tot, float(sum(p.n for p in full.problems))))
+    dist.destroy_process_group()
+
+
+def test_bands_sharded_across_two_ranks_gloo():
+    """Every band is owned by exactly one rank, each rank's workload is its block of the full
+    set with the global band indices as Philox keys, and the reduced count is the whole
+    set's."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    procs = [ctx.Process(target=_band_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    owned = out[0][1]
+    assert sorted(sum(owned, [])) == list(range(7)) and owned == out[1][1]
+    assert all(o[2] == 4.0 for o in out)            # slowest rank
+    assert all(o[3] == o[4] for o in out)           # every band counted once
