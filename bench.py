@@ -11,7 +11,8 @@ batched metric evaluation plus every NUTS leaf and initial point).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Under torchrun each rank runs its own independent problem (weak scaling, no
-data-path collective); rank 0 prints one JSON line.
+data-path collective), and the extras split the 64 batched bands across the ranks
+(each rank a contiguous block, no exchange); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -33,11 +34,13 @@ METRIC = "component*sample logL+grad evals/s"
 UNIT = "cs-evals/s"
 OPS_PER_CS = {0: 9.0, 1: 14.0}   # algorithmic FP32 lane-ops per component*sample (fwd+adj)
 FP32_LANES_PER_SM = 128
-N_SM = 148
 # DRAM bytes (read + write) per particle of one NUTS launch, from an ncu capture of the
-# same kernel on a 1024-particle launch of this workload (571 KB / 1024 particles);
-# traffic scales with the particle count (z rows in and out; the samples stay in L2)
+# same kernel on a 1024-particle launch of this workload (profiles/k_nuts_pulse_n16384_p1024.md);
+# traffic scales with the particle count (z rows in and out; the samples stay in L2).
+# None when the kernel has changed since the capture.
 NUTS_DRAM_BYTES_PER_PARTICLE = 557.75
+NUTS_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of a 1024-particle launch, scaled per "
+                     "particle (profiles/k_nuts_pulse_n16384_p1024.md)")
 
 
 def _args():
@@ -269,6 +272,40 @@ def measure_extras(stream):
         res["oracle_logz"] = float(gz.mean())
         res["fp64_over_mixed_wall"] = res["fp64"]["wall_s_per_run"] / res["mixed"]["wall_s_per_run"]
         out["smc_equal_error_pulse_n1024_p512"] = res
+    # (2a) single-channel Galactic-binary band at full size: N = 2^18 at dt = 15 s,
+    # K_true = 10, K_max = 30, P = 4096: logL+grad (mixed and FP64), one NUTS transition
+    # and one whole SMC stage from the prior start (mixed)
+    wg = synth.gb_band_k10()
+    zg, Kg = synth.prior_population(wg, 3)
+    zdg, Kdg = torch.as_tensor(zg, device="cuda"), torch.as_tensor(Kg, device="cuda")
+    csg = float(Kg.astype(np.float64).sum()) * wg.problems[0].n
+    bg = torch.tensor([0.5], dtype=torch.float64, device="cuda")
+    gbr = {"workload": wg.name, "unit": UNIT}
+    for name, prec in (("mixed", capi.MIXED), ("fp64", capi.FP64)):
+        ctx = sampler.open_context(wg, prec, stream=stream)
+        ctx.set_population(zdg, Kdg, beta=[1e-3])
+        gg = torch.empty_like(zdg)
+        ctx.eval(zdg, Kdg, bg, grad=True, g=gg)
+        msg = min(_events_ms(stream, lambda: ctx.eval(zdg, Kdg, bg, grad=True, g=gg))
+                  for _ in range(3 if prec == capi.MIXED else 1))
+        gbr[f"logl_grad_kernel_{name}"] = csg / (msg * 1e-3)
+        if prec == capi.MIXED:
+            ctx.update_metric()
+            ctx.counters(reset=True)
+            msn = _events_ms(stream, lambda: ctx.nuts_move(0, 0))
+            (_, cng, _, _), _ = ctx.counters(reset=True)
+            gbr["nuts_transition_mixed"] = cng / (msn * 1e-3)
+            gbr["nuts_ms_mixed"] = msn
+            ctx.init_population()
+            ctx.counters(reset=True)
+            mss = _events_ms(stream, lambda: ctx.run_stage(0, use_graph=True, read=False))
+            (ce, cn, _, _), _ = ctx.counters(reset=True)
+            gbr["stage_ms_mixed"] = mss
+            gbr["stage_mixed"] = (ce + cn) / (mss * 1e-3)
+        ctx.close()
+    gbr["mixed_over_fp64_logl_grad"] = (gbr["logl_grad_kernel_mixed"]
+                                        / gbr["logl_grad_kernel_fp64"])
+    out["gb_band_n262144_k10_p4096"] = gbr
     # (2b) two channels A and E (eq. gw_likelihood, flat PSD, simplified response):
     # 2^18 samples per channel, K_max = 30, P = 4096, logL + gradient and one NUTS round;
     # the value counts K_p x 2^19 component*samples (both channels)
@@ -295,12 +332,7 @@ def measure_extras(stream):
     best = autotune.tune(w5, capi.MIXED, nuts=False)
     ctx = sampler.open_context(w5, capi.MIXED, stream=stream, threads=best["threads"],
                                samples_per_thread=best["samples_per_thread"])
-    zs, Ks = [], []
-    for b in range(nb):
-        zb, Kb = synth.prior_population(w5, 100 + b, w5.P)
-        zs.append(zb)
-        Ks.append(Kb)
-    z5, K5 = np.concatenate(zs), np.concatenate(Ks)
+    z5, K5 = band_population(w5, range(nb))
     zd5, Kd5 = torch.as_tensor(z5, device="cuda"), torch.as_tensor(K5, device="cuda")
     ctx.set_population(zd5, Kd5, beta=[1e-3] * nb)
     b5 = torch.full((nb,), 0.5, dtype=torch.float64, device="cuda")
@@ -345,10 +377,80 @@ def measure_extras(stream):
     return out
 
 
+def _snapshot(ctx):
+    """Device copies of the population and the per-problem state a stage starts from."""
+    z, K, _, _ = ctx.get_population()
+    beta, logz, _ = ctx.temper_state()
+    eps, minv = ctx.get_kernel_params()
+    return dict(z=z.clone(), K=K.clone(), beta=beta, logz=logz, eps=eps, minv=minv)
+
+
+def _restore(ctx, snap):
+    ctx.set_population(snap["z"].clone(), snap["K"].clone(), beta=snap["beta"],
+                       logz=snap["logz"])
+    ctx.set_kernel_params(snap["eps"], snap["minv"])
+    ctx.sync()
+
+
+def band_population(full, bands):
+    """Frozen prior populations of the batched bands (seed 100 + global band index)."""
+    from paper_2609_17674_b300 import synth
+
+    zs, Ks = [], []
+    for b in bands:
+        zb, Kb = synth.prior_population(full, 100 + b, full.P)
+        zs.append(zb)
+        Ks.append(Kb)
+    return np.concatenate(zs), np.concatenate(Ks)
+
+
+def measure_sharded_bands(stream, world, rank, local, barrier):
+    """The 64 batched bands split across the ranks (each rank a contiguous block, its own
+    context, no exchange): logL+grad and one NUTS transition per rank, the whole job's
+    component*samples over the slowest rank's time (strong scaling: the total is fixed)."""
+    import torch
+
+    from paper_2609_17674_b300 import capi, sampler, synth
+    from paper_2609_17674_b300 import dist as tdist
+
+    full = synth.gb_bands()
+    wl, idx = tdist.shard_problems(full, world, rank)
+    dev = torch.device("cuda", local)
+    ms_e = ms_n = cs_e = cs_n = 0.0
+    if wl is not None:
+        z, K = band_population(full, idx)
+        zd, Kd = torch.as_tensor(z, device=dev), torch.as_tensor(K, device=dev)
+        ctx = sampler.open_context(wl, capi.MIXED, stream=stream)
+        ctx.set_population(zd, Kd, beta=[1e-3] * len(idx))
+        ctx.update_metric()
+        bt = torch.full((len(idx),), 0.5, dtype=torch.float64, device=dev)
+        g = torch.empty_like(zd)
+        ctx.eval(zd, Kd, bt, grad=True, g=g)
+        barrier()
+        ms_e = _events_ms(stream, lambda: ctx.eval(zd, Kd, bt, grad=True, g=g))
+        cs_e = float(sum(K[i * wl.P:(i + 1) * wl.P].astype(np.float64).sum() * wl.problems[i].n
+                         for i in range(len(idx))))
+        ctx.counters(reset=True)
+        barrier()
+        ms_n = _events_ms(stream, lambda: ctx.nuts_move(0, 0))
+        (_, c_n, _, _), _ = ctx.counters(reset=True)
+        cs_n = float(c_n)
+        ctx.close()
+    else:
+        barrier()
+        barrier()
+    me, ce = tdist.reduce_measurement(ms_e, cs_e, device=dev)
+    mn, cn = tdist.reduce_measurement(ms_n, cs_n, device=dev)
+    return {"workload": full.name, "ranks": world, "bands_per_rank": len(idx),
+            "unit": UNIT, "logl_grad_kernel": ce / (me * 1e-3),
+            "nuts_transition": cn / (mn * 1e-3), "scaling": "strong (64 bands in total)"}
+
+
 def run_gpu(a):
     import torch
 
     from paper_2609_17674_b300 import capi, sampler
+    from paper_2609_17674_b300 import dist as tdist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -364,18 +466,13 @@ def run_gpu(a):
         if dist is not None:
             dist.barrier()
 
-    def reduce(x, op):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=op)
-        return float(t.item())
-
+    props = torch.cuda.get_device_properties(local)
     wl = workload(rank, a.particles, a.samples)
     stream = torch.cuda.Stream()
     ctx = sampler.open_context(wl, capi.MIXED, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx.init_population()
+    ctx.profile(True, events=200 * a.steps)
     stage = 0
     for _ in range(a.warmup):   # the same calls as a timed step (first use loads their kernels)
         with torch.cuda.stream(stream):
@@ -383,7 +480,8 @@ def run_gpu(a):
         ctx.run_stage(stage, use_graph=False, read=False)
         stage += 1
     torch.cuda.synchronize()
-    ctx.profile(True, events=200 * a.steps)
+    stage0 = stage
+    snap = _snapshot(ctx)     # the state both legs start from: the same stage window
     ctx.counters(reset=True)
     ctx.profile_read(reset=True)
     clocks = ClockSampler(local, a.clock_ms, a.clock_fields)
@@ -395,7 +493,9 @@ def run_gpu(a):
     for _ in range(a.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)          # L2 flush between steps (256 MB write)
-        ctx.run_stage(stage, use_graph=False, read=False)   # queued: no host sync per stage
+        # eager launches with an event pair around each kernel (the per-kernel times of the
+        # roofline come from this same region); queued: no host sync per stage
+        ctx.run_stage(stage, use_graph=False, read=False)
         stage += 1
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -405,84 +505,96 @@ def run_gpu(a):
     ms = ev0.elapsed_time(ev1)
     (cs_eval, cs_nuts, cc_eval, cc_nuts), launches = ctx.counters(reset=True)
     prof = ctx.profile_read(reset=True)
-    ctx.profile(False)
-    from paper_2609_17674_b300 import dist as tdist
-
     ms_max, cs_total = tdist.reduce_measurement(ms, float(cs_eval + cs_nuts),
                                                 device=torch.device("cuda", local))
+    _, cc_total = tdist.reduce_measurement(ms, float(cc_eval + cc_nuts),
+                                           device=torch.device("cuda", local))
     value = cs_total / (ms_max * 1e-3)
+    value_computed = cc_total / (ms_max * 1e-3)
 
-    # roofline of the dominant kernel (NUTS transition), ALU bound (FP32 pipe)
+    # roofline of the dominant kernel (NUTS transition), ALU bound (FP32 pipe), on the
+    # component*samples it computed (the support window skips the rest)
     n_nuts, ms_nuts = prof["nuts"]
     per_launch_ms = ms_nuts / max(n_nuts, 1)
-    ops = OPS_PER_CS[wl.model] * cc_nuts       # component*samples the kernel computed
+    ops = OPS_PER_CS[wl.model] * cc_nuts
     achieved = ops / max(ms_nuts * 1e-3, 1e-12) / 1e12
     mhz = clk.get("sm_mhz") or 2032.0
-    peak = FP32_LANES_PER_SM * N_SM * mhz * 1e6 / 1e12
+    n_sm = props.multi_processor_count
+    peak = FP32_LANES_PER_SM * n_sm * mhz * 1e6 / 1e12
     roof = {"kernel": "k_nuts<PULSE,MIXED,32>", "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "Tops/s (FP32 lane-ops, FMA=1)", "frac": achieved / peak,
-            "traffic": NUTS_DRAM_BYTES_PER_PARTICLE * a.particles,
-            "traffic_note": "ncu dram__bytes_read+write of a 1024-particle launch, scaled per particle",
+            "traffic": NUTS_DRAM_BYTES_PER_PARTICLE * a.particles if NUTS_DRAM_BYTES_PER_PARTICLE
+            else None,
+            "traffic_note": NUTS_TRAFFIC_NOTE,
             "launches": n_nuts, "ms_per_launch": per_launch_ms,
-            "share_of_step": ms_nuts / ms, "peak_basis": f"128 FP32 lanes x 148 SMs x {mhz:.0f} MHz"
-                                                         " (median SM clock during the timed region)",
+            "share_of_step": ms_nuts / ms,
+            "peak_basis": f"128 FP32 lanes x {n_sm} SMs (device properties) x {mhz:.0f} MHz "
+                          "(median SM clock sampled during the timed region)",
             "ops_per_cs": OPS_PER_CS[wl.model],
+            "work_basis": "component*samples the NUTS launches computed (device counter)",
             "cs_nominal": cs_nuts, "cs_computed": cc_nuts,
+            "computed_cs_per_s": cc_nuts / max(ms_nuts * 1e-3, 1e-12),
             "nominal_cs_per_s": cs_nuts / max(ms_nuts * 1e-3, 1e-12),
             "kernels_ms": {k: v[1] for k, v in prof.items()}}
 
-    # end to end: population resident on the host between stages (pinned buffers)
+    # end to end through the public API with the population on the host (pinned) between
+    # stages, over the same stage window from the same starting state and in the same
+    # execution mode (eager, per-kernel events) as the device-timed region
     e2e = None
     if not a.no_e2e:
-        z, K, _, ln = ctx.get_population()
-        zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
-        Kh = torch.empty(K.shape, dtype=K.dtype, pin_memory=True)
-        lnh = torch.empty(ln.shape, dtype=ln.dtype, pin_memory=True)
-        zh.copy_(z)
-        Kh.copy_(K)
-        eps, _ = ctx.get_kernel_params()
-        beta_h = np.array([betas[-1]])
-        logz_h = np.zeros(1)
-        zd, Kd = torch.empty_like(z), torch.empty_like(K)
-        nsteps = max(2, a.steps // 2)
+        _restore(ctx, snap)
+        zh = torch.empty(snap["z"].shape, dtype=snap["z"].dtype, pin_memory=True)
+        Kh = torch.empty(snap["K"].shape, dtype=snap["K"].dtype, pin_memory=True)
+        lnh = torch.empty(snap["K"].shape, dtype=torch.float64, pin_memory=True)
+        zh.copy_(snap["z"])
+        Kh.copy_(snap["K"])
+        zd, Kd = torch.empty_like(snap["z"]), torch.empty_like(snap["K"])
+        state = dict(eps=snap["eps"], beta=snap["beta"], logz=snap["logz"])
 
-        def e2e_step(st, eps, beta_h, logz_h):
+        def e2e_step(st):
             with torch.cuda.stream(stream):
                 zd.copy_(zh, non_blocking=True)
                 Kd.copy_(Kh, non_blocking=True)
-            ctx.set_population(zd, Kd, beta=beta_h, logz=logz_h)
-            ctx.set_kernel_params(eps)
-            b, lz, _ = ctx.run_stage(st, use_graph=True)
+            ctx.set_population(zd, Kd, beta=state["beta"], logz=state["logz"])
+            ctx.set_kernel_params(state["eps"])
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            b, lz, _ = ctx.run_stage(st, use_graph=False)
             zo, Ko, _, lno = ctx.get_population()
             with torch.cuda.stream(stream):
                 zh.copy_(zo, non_blocking=True)
                 Kh.copy_(Ko, non_blocking=True)
                 lnh.copy_(lno, non_blocking=True)
-            eps, _ = ctx.get_kernel_params()
+            state["eps"], _ = ctx.get_kernel_params()
             stream.synchronize()
-            return eps, b, lz
+            state["beta"], state["logz"] = b, lz
 
-        # one untimed step: captures the stage graph and loads the copy paths
-        eps, beta_h, logz_h = e2e_step(stage, eps, beta_h, logz_h)
-        stage += 1
         ctx.counters(reset=True)
+        ctx.profile_read(reset=True)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(nsteps):
-            eps, beta_h, logz_h = e2e_step(stage, eps, beta_h, logz_h)
-            stage += 1
+        for st in range(stage0, stage0 + a.steps):
+            e2e_step(st)
         t1 = time.perf_counter()
         barrier()
         (ce, cn, _, _), _ = ctx.counters(reset=True)
-        el = reduce(t1 - t0, dist.ReduceOp.MAX if dist else None)
-        cst = reduce(float(ce + cn), dist.ReduceOp.SUM if dist else None)
+        ctx.profile_read(reset=True)
+        el, cst = tdist.reduce_measurement((t1 - t0) * 1e3, float(ce + cn),
+                                           device=torch.device("cuda", local))
         h2d = zh.numel() * 8 + Kh.numel() * 4 + 8 * 4
         d2h = zh.numel() * 8 + Kh.numel() * 4 + lnh.numel() * 8 + 8 * 5
-        e2e = {"value": cst / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h,
-               "path": "pinned host population -> tsmc_set_population -> tsmc_run_stage (graph)"
-                       " -> tsmc_get_population -> pinned host"}
+        e2e = {"value": cst / (el * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "stages": [stage0, stage0 + a.steps],
+               "path": "pinned host population -> tsmc_set_population -> tsmc_run_stage "
+                       "(eager, per-kernel events, as the device-timed region) -> "
+                       "tsmc_get_population -> pinned host; same stages and starting state "
+                       "as the device-timed region"}
+    ctx.profile(False)
+
+    sharded = None
+    if world > 1 and not a.no_extras:
+        sharded = measure_sharded_bands(stream, world, rank, local, barrier)
 
     if rank != 0:
         if dist is not None:
@@ -498,20 +610,28 @@ def run_gpu(a):
                          "processes): logL+grad, metric, one RJ move and one NUTS transition "
                          f"each; {busy:.1f} s"}
     extras = None if a.no_extras else measure_extras(stream)
+    if extras is not None and sharded is not None:
+        extras["gb_bands_sharded"] = sharded
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "value_computed": value_computed,
+        "value_basis": "value: every K_p*N component*sample of each logL+grad evaluation "
+                       "(the metric's definition); value_computed: the component*samples "
+                       "the kernels computed (the support window skips terms < 2^-26 A); "
+                       "the roofline uses the computed work",
         "config": {"workload": wl.name + " (SMC stage: ESS bisection, resampling, metric, "
                                          "5 x [RJ birth/death + NUTS depth<=6])",
                    "N": a.samples, "P": a.particles, "kmax": 40, "K_true": 20,
                    "precision": "mixed: FP32 templates/residuals, FP64 sums/anchors/log-weights",
                    "l2": "flushed between steps (256 MB write)",
-                   "pulse_window": "on: (component, warp range) pairs with |t - t0| > 6 w (every term < 2^-26 A) "
-                                   "skipped; value counts every K_p*N component*sample",
+                   "mode": "eager launches, an event pair per kernel (no CUDA graph)",
+                   "pulse_window": "on: (component, warp range) pairs with |t - t0| > 6 w "
+                                   "(every term < 2^-26 A) skipped",
                    "computed_fraction": (cc_eval + cc_nuts) / max(cs_eval + cs_nuts, 1),
                    "parallelism": f"{world} independent problem(s), one per GPU",
-                   "stages": [stage - a.steps - (max(2, a.steps // 2) + 1 if e2e else 0), stage],
+                   "stages": [stage0, stage0 + a.steps],
                    "beta_end": betas[-1]},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk, "extras": extras,
