@@ -80,6 +80,7 @@ def lib():
             "orc_leapfrog": (None, [P, P, I32, D, D, P, P, P, P, P]),
             "orc_temper": (None, [I32, P, D, D, P, P, P, P]),
             "orc_resample": (None, [P, I32, I32, I32, P, P]),
+            "orc_resample_scale": (I32, [I32]),
             "orc_metric": (None, [P, P, P, P, I32, D, P]),
             "orc_eps_update": (D, [D, D]),
             "orc_eps_initial": (D, [P]),

@@ -699,25 +699,40 @@ void orc_temper(int32_t P, const double* ell, double alpha, double beta, double*
 }
 
 /* ------------------------------------------------------------------------- */
-/* Systematic resampling: W_i = exp(logw_i - max), C its inclusive prefix sum, */
-/* one U ~ (0,1) per (problem, stage); ancestor a_i = min{j : C_j > (i+U)/P C_P}*/
-/* The resampling step of Sec. 2 (its scheme is not stated there).            */
+/* Systematic resampling, the resampling step of Sec. 2 (its scheme is not    */
+/* stated there).  The weights are quantised to integers,                      */
+/*   W_i = round(exp(logw_i - max) 2^S),  S = 52 - ceil(log2 P),               */
+/* so that every inclusive prefix sum C_j is an exact integer <= 2^52 (a     */
+/* weight below 2^-(S+1) of the largest counts as zero).  One U ~ (0,1) per    */
+/* (problem, stage); with t_i = (i + U) / P C_P, at most C_P - 1, the          */
+/* ancestor is a_i = min{j : C_j > t_i}.                                       */
 /* ------------------------------------------------------------------------- */
+int32_t orc_resample_scale(int32_t P) {
+  int32_t S = 52;
+  for (int64_t q = 1; q < (int64_t)P; q <<= 1) --S;
+  return S;
+}
+
 void orc_resample(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
                   const double* logw, int32_t* ancestors) {
   double m = -INFINITY;
   for (int32_t i = 0; i < P; ++i) if (logw[i] > m) m = logw[i];
-  double* C = (double*)malloc(sizeof(double) * (size_t)P);
-  double run = 0.0;
-  for (int32_t i = 0; i < P; ++i) { run += exp(logw[i] - m); C[i] = run; }
+  const int32_t S = orc_resample_scale(P);
+  int64_t* C = (int64_t*)malloc(sizeof(int64_t) * (size_t)P);
+  int64_t run = 0;
+  for (int32_t i = 0; i < P; ++i) {
+    run += (int64_t)llrint(ldexp(exp(logw[i] - m), S));
+    C[i] = run;
+  }
   uint64_t w[4];
   draw(c, problem, 0, stage, 0, ORC_PU_RESAMPLE, 0, w);
   const double U = orc_u01(w[0]);
-  const double total = C[P - 1];
+  const double total = (double)C[P - 1];
   int32_t j = 0;
   for (int32_t i = 0; i < P; ++i) {
     double target = ((double)i + U) / (double)P * total;
-    while (j < P - 1 && !(C[j] > target)) ++j;
+    if (target > total - 1.0) target = total - 1.0;
+    while (j < P - 1 && !((double)C[j] > target)) ++j;
     ancestors[i] = j;
   }
   free(C);

@@ -137,6 +137,7 @@ void orc_temper(int32_t P, const double* ell, double alpha, double beta, double*
                 double* logz_inc, double* ess, double* logw);
 
 /* systematic resampling: ancestors[i] for i < P */
+int32_t orc_resample_scale(int32_t P);
 void orc_resample(const orc_cfg* c, int32_t problem, int32_t stage, int32_t P,
                   const double* logw, int32_t* ancestors);
 

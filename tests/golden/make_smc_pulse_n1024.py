@@ -3,8 +3,9 @@
 Calls only the oracle (and the shared input generator).  Each run is a prior-start
 SMC (P=512, K ~ U{0..10}, alpha=0.5, 5 rounds of RJ + NUTS per stage) with Philox
 seed s; the data are the same for every run.  Stored per run: the K histogram of
-the final population, log Z, the stage count, and label-invariant summaries
-(mean K; mean sorted pulse centres and amplitudes for particles with K = K_true).
+the final population, log Z, the stage count, beta and log Z after every stage, and
+label-invariant summaries (mean K; mean sorted pulse centres and amplitudes for
+particles with K = K_true).
 Run:  python tests/golden/make_smc_pulse_n1024.py   (about 5 minutes on 8 cores)
 """
 import json
@@ -46,7 +47,8 @@ def run(seed):
     res = oracle.Oracle(wl).smc_run(wl.P, max_stages=400)
     s = summaries(wl, res["z"], res["K"])
     s.update(seed=seed, logz=float(res["logz"]), n_stages=int(res["n_stages"]),
-             beta_last=float(res["beta"][-1]))
+             beta_last=float(res["beta"][-1]), beta_hist=[float(b) for b in res["beta"]],
+             logz_hist=[float(x) for x in res["logz_hist"]])
     return s
 
 

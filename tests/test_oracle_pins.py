@@ -6,6 +6,7 @@ Gaussians, geometric sums of sinusoids, linear-Gaussian evidence), finite
 differences, brute-force quadrature of the K posterior, stationarity of the
 kernels, and textbook properties of ESS bisection and systematic resampling.
 """
+import itertools
 import math
 
 import numpy as np
@@ -573,6 +574,36 @@ def test_resample_properties():
     W /= W.sum()
     counts = np.bincount(a, minlength=P)
     assert np.all(counts >= np.floor(P * W) - 1e-9) and np.all(counts <= np.ceil(P * W) + 1e-9)
+
+
+@pytest.mark.parametrize("P,spread", [(1, 1.0), (7, 0.5), (512, 3.0), (3000, 8.0)])
+def test_resample_ancestors_by_exact_integer_prefix_sums(P, spread):
+    """Systematic resampling on quantised weights, written out with Python integers (exact
+    prefix sums) and the same double-precision target: W_i = round(exp(logw_i - max) 2^S),
+    S = 52 - ceil(log2 P), t_i = min((i + U) / P C_P, C_P - 1), a_i = min{j : C_j > t_i}.
+    Weights that underflow the quantum and -inf log-weights are never chosen."""
+    wl = synth.pulse_n1024_k3()
+    o = oracle.Oracle(wl)
+    rng = np.random.default_rng(P)
+    logw = rng.normal(0.0, spread, P)
+    if P > 4:
+        logw[1] = -np.inf
+        logw[3] = logw.max() - 80.0          # below 2^-(S+1) of the largest weight
+    S = 52 - (P - 1).bit_length()
+    assert oracle.lib().orc_resample_scale(P) == S
+    m = max(logw)
+    Wq = [0 if x == -np.inf else int(round(math.ldexp(math.exp(x - m), S))) for x in logw]
+    C = list(itertools.accumulate(Wq))
+    assert C[-1] <= 2 ** 52
+    u = oracle.u01(oracle.philox([0, 3, 7, 0], [wl.seed, 0])[0])
+    expect = []
+    for i in range(P):
+        t = min((float(i) + u) / float(P) * float(C[-1]), float(C[-1]) - 1.0)
+        expect.append(next(j for j in range(P) if float(C[j]) > t))
+    got = o.resample(3, logw)
+    assert got.tolist() == expect
+    if P > 4:
+        assert 1 not in expect and 3 not in expect
 
 
 def test_init_population_draws_the_prior():
