@@ -201,8 +201,10 @@ tsmc_status tsmc_get_birth_proposal(tsmc_ctx* ctx, int32_t problem, double* out_
 tsmc_status tsmc_update_metric(tsmc_ctx* ctx);
 
 /* Choose beta by ESS bisection, reweight (evidence increment) and resample
- * systematically (Sec. 2 steps 1-2).  Host outputs (nullable) [n_problems]; with
- * all three NULL the call does not synchronise. */
+ * systematically (Sec. 2 steps 1-2).  Systematic resampling runs on weights quantised
+ * to integers, round(exp(logw - max) 2^S) with S = 52 - ceil(log2 P), whose prefix sums
+ * are exact; ancestor i is the first j with C_j > min((i + U) / P C_P, C_P - 1).  Host
+ * outputs (nullable) [n_problems]; with all three NULL the call does not synchronise. */
 tsmc_status tsmc_temper_reweight_resample(tsmc_ctx* ctx, int32_t stage, double* beta_host,
                                           double* logz_host, double* ess_host);
 /* Current beta, log Z and last ESS per problem (host [n_problems], nullable);
@@ -266,8 +268,9 @@ tsmc_status tsmc_profile_read(tsmc_ctx* ctx, int64_t* launches_host, double* ms_
  *
  *   logw_dev       [n_problems * particles] FP64 log-weights (any finite shift)
  *   ancestors_dev  [n_problems * particles] int32 output, local indices per problem:
- *                  a_i = min{j : C_j > (i + U) / P C_P}, C the prefix sums of
- *                  exp(logw - max), U from Philox key (seed, problem), counter
+ *                  a_i = min{j : C_j > min((i + U) / P C_P, C_P - 1)}, C the exact
+ *                  integer prefix sums of round(exp(logw - max) 2^S), S = 52 -
+ *                  ceil(log2 P), U from Philox key (seed, problem), counter
  *                  (0, stage, purpose 7, 0) -- the same draw and arithmetic as the
  *                  context path, so the results are identical.
  *   cuda_stream    cudaStream_t the kernel is launched on (NULL: legacy stream).

@@ -208,6 +208,7 @@ KParams kparams(Ctx* c) {
 SmemPlan smem_plan(Ctx* c, bool fisher, int depth) {
   SmemPlan sp;
   sp.kd = c->kd;
+  sp.kmax = c->cfg.kmax;
   sp.nw = c->T / 32;
   sp.depth = depth;
   sp.fisher = fisher;
@@ -219,6 +220,10 @@ SmemPlan smem_plan(Ctx* c, bool fisher, int depth) {
 // kernel variant, up to the device limit, before any launch (and before graph capture).
 int g_smem_optin = 0;
 
+// The particle kernels also prefer the largest shared-memory carveout of the unified
+// L1/shared array: measured on the pulse workload (N = 16384, K_max = 40), the NUTS
+// kernel with 26 KB per block ran 5% slower with the driver's default carveout (which
+// keeps more L1: the FP32 samples then hit L1 instead of L2) than with the maximum one.
 template <typename F>
 tsmc_status allow_smem(Ctx* c, F* fn) {
   if (!g_smem_optin) {
@@ -226,6 +231,8 @@ tsmc_status allow_smem(Ctx* c, F* fn) {
     TRY_CUDA(c, cudaGetDevice(&dev));
     TRY_CUDA(c, cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   }
+  TRY_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared));
   return cuda_check(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             g_smem_optin - 2048),
                     "cudaFuncSetAttribute");
@@ -244,7 +251,8 @@ tsmc_status prep_t(Ctx* c) {
   TRY(allow_smem(c, &k_eval<MODEL, PREC, R, true, false>));
   TRY(allow_smem(c, &k_eval<MODEL, PREC, R, false, false>));
   TRY(allow_smem(c, &k_rj<MODEL, PREC, R>));
-  TRY(allow_smem(c, &k_nuts<MODEL, PREC, R>));
+  if constexpr (PREC == FP64) TRY(allow_smem(c, &k_nuts<MODEL, PREC, R>));
+  else TRY(allow_smem(c, &k_nuts_mixed<MODEL, R>));
   return TSMC_OK;
 }
 
@@ -337,12 +345,21 @@ tsmc_status nuts_launch_t(Ctx* c, int round, NutsOut out) {
   KParams kp = kparams(c);
   kp.order = c->order;
   SmemPlan sp = smem_plan(c, false, c->cfg.max_depth);
-  const size_t sm = sp.nuts_kernel_bytes();
-  auto fn = &k_nuts<MODEL, PREC, R>;
-  TRY(launch_prep(c, fn, sm));
-  pre(c, KC_NUTS);
-  fn<<<(unsigned)c->Ptot, c->T, sm, c->stream>>>(kp, round, out, sp);
-  return last_launch(c, "k_nuts");
+  if constexpr (PREC == FP64) {
+    const size_t sm = sp.nuts_kernel_bytes();
+    auto fn = &k_nuts<MODEL, PREC, R>;
+    TRY(launch_prep(c, fn, sm));
+    pre(c, KC_NUTS);
+    fn<<<(unsigned)c->Ptot, c->T, sm, c->stream>>>(kp, round, out, sp);
+    return last_launch(c, "k_nuts");
+  } else {
+    const size_t sm = sp.nuts_mixed_kernel_bytes();
+    auto fn = &k_nuts_mixed<MODEL, R>;
+    TRY(launch_prep(c, fn, sm));
+    pre(c, KC_NUTS);
+    fn<<<(unsigned)c->Ptot, c->T, sm, c->stream>>>(kp, round, out, sp);
+    return last_launch(c, "k_nuts_mixed");
+  }
 }
 
 #define DISPATCH(FN, ...)                                                                 \
@@ -458,8 +475,8 @@ tsmc_status temper_resample(Ctx* c, int stage) {
     TRY(last_launch(c, "k_temper"));
   }
   pre(c, KC_RESAMPLE);
-  k_resample<<<np, tt, 0, c->stream>>>(c->logw, c->cw, c->anc, c->probs, c->cfg.seed, stage, P,
-                                       c->cfg.problem_base);
+  k_resample<<<np, tt, 0, c->stream>>>(c->logw, reinterpret_cast<long long*>(c->cw), c->anc,
+                                       c->probs, c->cfg.seed, stage, P, c->cfg.problem_base);
   TRY(last_launch(c, "k_resample"));
   const int64_t work = c->Ptot * (c->kd + 1);
   const int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 16);
@@ -654,6 +671,7 @@ tsmc_status tsmc_set_problem(tsmc_ctx* ctx, int32_t problem, const double* d_hos
   }
   pd.f_to = split_df(t_origin);
   pd.f_dt = split_df(dt);
+  pd.f_is2 = split_df(pd.inv_s2);
   pd.nch = c->cfg.channels == 2 ? 2 : 1;
   pd.nc = n / pd.nch;
   for (int q = 0; q < 4; ++q) {
@@ -1006,26 +1024,26 @@ tsmc_status tsmc_profile_read(tsmc_ctx* ctx, int64_t* launches_host, double* ms_
 }
 
 // ---------------------------------------------------------------------------
-// Allocation-free systematic resampling.  Scratch (the FP64 prefix sums and a
+// Allocation-free systematic resampling.  Scratch (the 64-bit prefix sums and a
 // block of all-zero problem descriptors, i.e. no problem marked done) lives in
 // file-scope device arrays that every GPU loading this library keeps until exit.
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
-#define TSMC_STATIC_MAX_PARTICLES 65536   /* n_problems * particles: 512 KB of prefix sums */
+#define TSMC_STATIC_MAX_PARTICLES 65536   /* n_problems * particles: 512 KB of 64-bit prefix sums */
 #define TSMC_STATIC_MAX_PROBLEMS 256
 
-static __device__ __align__(256) double g_static_prefix[TSMC_STATIC_MAX_PARTICLES];
+static __device__ __align__(256) long long g_static_prefix[TSMC_STATIC_MAX_PARTICLES];
 static __device__ __align__(256) ProbDev g_static_probs[TSMC_STATIC_MAX_PROBLEMS];
 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-double* g_static_prefix_dev[kMaxDevices] = {};
+long long* g_static_prefix_dev[kMaxDevices] = {};
 ProbDev* g_static_probs_dev[kMaxDevices] = {};
 
 // device addresses of the static arrays for the current device (looked up once per device)
-tsmc_status static_scratch(double** prefix, ProbDev** probs) {
+tsmc_status static_scratch(long long** prefix, ProbDev** probs) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, TSMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -1040,7 +1058,7 @@ tsmc_status static_scratch(double** prefix, ProbDev** probs) {
     e = cudaGetSymbolAddress(&b, g_static_probs);
     if (e != cudaSuccess)
       return fail(nullptr, TSMC_ECUDA, std::string("cudaGetSymbolAddress(problems): ") + cudaGetErrorString(e));
-    g_static_prefix_dev[dev] = static_cast<double*>(a);
+    g_static_prefix_dev[dev] = static_cast<long long*>(a);
     g_static_probs_dev[dev] = static_cast<ProbDev*>(b);
   }
   *prefix = g_static_prefix_dev[dev];
@@ -1062,7 +1080,7 @@ tsmc_status tsmc_resample_systematic_static(const double* logw_dev, int32_t n_pr
   if ((int64_t)n_problems * particles > TSMC_STATIC_MAX_PARTICLES)
     return fail(nullptr, TSMC_EINVAL,
                 "n_problems * particles above the static scratch limit of 65536");
-  double* prefix = nullptr;
+  long long* prefix = nullptr;
   ProbDev* probs = nullptr;
   TRY(static_scratch(&prefix, &probs));
   const int tt = particles >= 1024 ? 1024 : ((particles + 31) / 32) * 32;

@@ -92,6 +92,8 @@ struct ProbDev {
   int32_t nch, pad_;
   double resp[4];
   float f_resp[4];
+  float2 f_is2;      // 1/sigma^2 as double-float
+  float2 pad2_;
 };
 
 // ---------------------------------------------------------------------------

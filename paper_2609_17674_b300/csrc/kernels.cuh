@@ -35,16 +35,26 @@ struct KParams {
 // Shared-memory carve for one particle block.
 struct SmemPlan {
   int kd;          // kmax * D
+  int kmax;        // component slots
   int nw;          // warps per block
   int depth;       // NUTS checkpoint levels (0 for non-NUTS kernels)
   bool fisher;
   int nch;         // data channels (mixed-path constants per channel)
   __host__ __device__ size_t eval_bytes() const {
-    return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 4 + 64) +
-           sizeof(float) * (size_t)kd * NCF * nch + 32;
+    return sizeof(double) * (4 * (size_t)kd + (size_t)nw * kd * (fisher ? 2 : 1) + 128 + 8 + 64) +
+           sizeof(float) * (size_t)kmax * NCF * nch + 32;
   }
   __host__ __device__ size_t nuts_bytes() const {
     return sizeof(double) * (size_t)kd * (14 + 2 * (size_t)(depth + 1));   // 8-byte slots
+  }
+  // mixed NUTS: 5 double-float position vectors, 9 FP32 vectors, 2 (depth + 1) FP32
+  // checkpoint rows, and the leaf uniforms of the largest subtree
+  __host__ __device__ size_t nuts_mixed_bytes() const {
+    return sizeof(float2) * 5 * (size_t)kd + sizeof(float) * (size_t)kd * (9 + 2 * (size_t)(depth + 1)) +
+           sizeof(float) * ((size_t)1 << (depth > 0 ? depth - 1 : 0)) + 16;
+  }
+  __host__ __device__ size_t nuts_mixed_kernel_bytes() const {
+    return eval_bytes() + nuts_mixed_bytes() + 64;
   }
   // eval kernel: + gradient and Gauss-Newton staging; RJ: + proposal coordinates
   __host__ __device__ size_t eval_kernel_bytes() const {
@@ -66,12 +76,12 @@ __device__ __forceinline__ EvalSmem carve_eval(char*& p, const SmemPlan& sp, con
   sm.wacc = d; d += (size_t)sp.nw * sp.kd;
   if (sp.fisher) { sm.wfis = d; d += (size_t)sp.nw * sp.kd; } else { sm.wfis = nullptr; }
   sm.red = d; d += 128;
-  sm.scal = d; d += 4;
+  sm.scal = d; d += 8;
   sm.exptab = reinterpret_cast<float2*>(d); d += 64;
   if (reinterpret_cast<uintptr_t>(d) & 8) d += 1;   // float4 loads of the constants
   sm.cf = reinterpret_cast<float*>(d);
-  sm.cfch = sp.kd * NCF;
-  p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kd * NCF * sp.nch);
+  sm.cfch = sp.kmax * NCF;
+  p = reinterpret_cast<char*>(sm.cf + (size_t)sp.kmax * NCF * sp.nch);
   // keep 8-byte alignment for what follows
   p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
   sm.tw = tw;
@@ -502,16 +512,13 @@ __global__ void k_kde_build(KParams kp, int32_t* kcum, double* kde_out, double f
 // ---------------------------------------------------------------------------
 // NUTS transition (Sec. 3.2): one block per particle.  Warps 0 and 1 run the tree
 // logic on the (K*D)-vectors in shared memory; every leapfrog calls the block-wide
-// evaluation.  Control values are broadcast through shared memory.
+// evaluation.  Control values are broadcast through shared memory.  k_nuts is the FP64
+// path (control in FP64, the oracle's arithmetic); k_nuts_mixed the mixed path.
 // ---------------------------------------------------------------------------
 struct NutsOut { double* acc; int32_t* nleaf; int32_t* flags; };
 
-// Tree-control arithmetic: FP64 on the FP64 path (bit-level agreement with the
-// oracle), FP32 on the mixed path (momenta, U-turn sums, kinetic energy and the
-// probabilities compared with uniforms; positions, H and log-weights stay FP64).
-__device__ __forceinline__ float ct_exp(float x) { return expf(x); }
+// Tree-control arithmetic of k_nuts: FP64 (bit-level agreement with the oracle).
 __device__ __forceinline__ double ct_exp(double x) { return exp(x); }
-__device__ __forceinline__ float ct_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double ct_log1p(double x) { return log1p(x); }
 
 template <typename CT>
@@ -531,19 +538,6 @@ __device__ __forceinline__ double momentum_normal<double>(uint64_t seed, int pro
                                                           int round, uint64_t m) {
   return draw_normal(seed, problem, particle, stage, round, PU_MOMENTUM, m);
 }
-template <>
-__device__ __forceinline__ float momentum_normal<float>(uint64_t seed, int problem,
-                                                        uint64_t particle, int stage, int round,
-                                                        uint64_t m) {
-  // same stream and Box-Muller pairing as the FP64 path, evaluated in FP32
-  const Rand4 r = draw(seed, problem, particle, stage, round, PU_MOMENTUM, m >> 2);
-  const int pair = (int)((m & 3) >> 1);
-  const float ua = (float)u01(r.w[2 * pair]), ub = (float)u01(r.w[2 * pair + 1]);
-  const float rad = sqrtf(-2.0f * logf(ua));
-  float sn, cs;
-  sincospif(2.0f * ub, &sn, &cs);
-  return (m & 1) ? rad * sn : rad * cs;
-}
 
 template <typename CT>
 __device__ __forceinline__ CT warp_dot_minv(const CT* a, const CT* b, const CT* minv, int n,
@@ -555,7 +549,8 @@ __device__ __forceinline__ CT warp_dot_minv(const CT* a, const CT* b, const CT* 
 
 template <int MODEL, int PREC, int R>
 __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, SmemPlan sp) {
-  using CT = typename std::conditional<PREC == MIXED, float, double>::type;
+  static_assert(PREC == FP64, "the mixed path runs k_nuts_mixed");
+  using CT = double;
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   __shared__ int s_flag[8];
@@ -607,7 +602,6 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   if (tid < 4) s_minv[tid] = (CT)kp.minv[4 * prob + tid];
   const CT* minv = s_minv;
   const double* zg = kp.z + gi * (int64_t)kd;
-  if (PREC == MIXED) init_block_tables(sm);
   for (int i = tid; i < n; i += blockDim.x) { zc[i] = zg[i]; z1[i] = zg[i]; }
   __syncthreads();
   double cs_done = 0.0;   // component*samples computed (thread 0)
@@ -646,8 +640,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
       de_c = (CT)de;
     }
     if (l >= 0) {   // leapfrog: half step in momentum, full step in position
-      // (the mixed path applies it element by element inside the evaluation's setup)
-      if (PREC == FP64 && warp == 0) {
+      if (warp == 0) {
         for (int i = lane; i < n; i += 32) {
           const CT ph = p1[i] + (CT)0.5 * de_c * g1[i];
           p1[i] = ph;
@@ -659,15 +652,9 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
                              (uint64_t)((nsub - 1) + l));
         s_uleaf = u01(w.w[0]);
       }
-      if (PREC == FP64) __syncthreads();
+      __syncthreads();
     }
-    if constexpr (PREC == MIXED) {
-      const LeapPre leap{p1, g1, z1, minv, de_c};
-      block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr,
-                                                  l >= 0 ? &leap : nullptr);
-    } else {
-      block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
-    }
+    block_eval<MODEL, PREC, R, true, false, CT>(pb, kp.pa, K, beta, z1, sm, g1, nullptr);
     if (tid == 0) cs_done += sm.scal[3];
     if (l < 0) {   // initial point: momentum, H0 and both trajectory ends
       if (warp == 0) {
@@ -813,6 +800,309 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
         atomicAdd(kp.cs_count + 1, (unsigned long long)n / D * (unsigned long long)pb.n *
                                        (unsigned long long)(leaves + 1));
         atomicAdd(kp.cs_count + 3, (unsigned long long)cs_done);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NUTS transition on the mixed path (Sec. 3.2): the tree of k_nuts (same moves, same
+// random stream) with no FP64 instruction per leaf.  Every FP64 warp instruction holds a
+// sub-partition's FP64 unit for tens of cycles on this part, and the per-leaf phases
+// that run beside the sample loop (setup, block totals, tree control) sit on each leaf's
+// critical path, so: positions are double-float pairs (converted from and to FP64 once per
+// transition), the energies H and the log-weights double-float, momenta, U-turn sums,
+// acceptance statistics and the probabilities compared with uniforms FP32, uniforms 24-bit.
+// The uniforms of a subtree's leaves are drawn in parallel when the subtree starts, the
+// direction bits and top-level uniforms of every depth when the transition starts.
+// ---------------------------------------------------------------------------
+// 24 random bits to the open interval (0, 1): ((x >> 40) + 1/2) 2^-24
+__device__ __forceinline__ float u01f(uint64_t x) {
+  return __fmaf_rn((float)(uint32_t)(x >> 40), 0x1p-24f, 0x1p-25f);
+}
+__device__ __forceinline__ bool df_gt(DF a, DF b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+// a + b for a double-float a and a float b (a non-finite a gives the plain sum)
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  if (!isfinite(a.hi)) return DF{a.hi + b, 0.f};
+  const DF s = two_sum(a.hi, b);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+// a - b rounded to FP32 (finite a, b)
+__device__ __forceinline__ float df_sub_f(DF a, DF b) { return df_add(a, df_neg(b)).hi; }
+// log(e^a + e^b) of double-float log-weights (hi = -inf: weight zero)
+__device__ __forceinline__ DF df_lae(DF a, DF b) {
+  if (a.hi == -INFINITY) return b;
+  if (b.hi == -INFINITY) return a;
+  const bool ab = df_gt(a, b);
+  const DF m = ab ? a : b, o = ab ? b : a;
+  return df_add_f(m, log1pf(expf(df_sub_f(o, m))));
+}
+// m-th standard normal of the momentum stream: the Box-Muller pairing of draw_normal, in FP32
+// from 24-bit uniforms
+__device__ __forceinline__ float momentum_normal_f(uint64_t seed, int problem, uint64_t particle,
+                                                   int stage, int round, uint64_t m) {
+  const Rand4 r = draw(seed, problem, particle, stage, round, PU_MOMENTUM, m >> 2);
+  const int pair = (int)((m & 3) >> 1);
+  const float ua = u01f(r.w[2 * pair]), ub = u01f(r.w[2 * pair + 1]);
+  const float rad = sqrtf(-2.0f * logf(ua));
+  float sn, cs;
+  sincospif(2.0f * ub, &sn, &cs);
+  return (m & 1) ? rad * sn : rad * cs;
+}
+
+template <int MODEL, int R>
+__global__ void __launch_bounds__(256, 2) k_nuts_mixed(KParams kp, int round, NutsOut out,
+                                                         SmemPlan sp) {
+  extern __shared__ __align__(16) char smem[];
+  constexpr int D = model_d<MODEL>();
+  __shared__ int s_flag[8];
+  // 0 H0, 1 log W of the trajectory, 3/4 ll_old/ll_new of the chosen point, 5 log W of the
+  // current subtree, 6/7 ll_old/ll_new of its candidate
+  __shared__ DF s_ctl[8];
+  __shared__ float s_acc;                 // sum over leaves of min(1, e^{H0 - H})
+  __shared__ float s_minv[4];
+  __shared__ int s_dir[kMaxDepth];
+  __shared__ float s_utop[kMaxDepth];
+  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
+  const int prob = (int)(gi / kp.P);
+  const int pkey = prob + kp.prob_base;
+  const uint64_t li = (uint64_t)(gi % kp.P);
+  __shared__ ProbDev s_pb;
+  const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
+  if (pb.done) return;
+  const int stage = *kp.stage;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = min(max(kp.K[gi], 0), kp.kmax);
+  const int n = K * D;
+  bool run = n > 0;
+  if (kp.schedule == 1) {
+    const Rand4 m = draw(kp.seed, pkey, li, stage, round, PU_MOVETYPE, 0);
+    run = run && (u01(m.w[0]) < kp.p_nuts);
+  }
+  if (!run) {
+    if (tid == 0) {
+      if (out.acc) out.acc[gi] = 0.0;
+      if (out.nleaf) out.nleaf[gi] = 0;
+      if (out.flags) out.flags[gi] = 0;
+    }
+    return;
+  }
+  char* p = smem;
+  EvalSmem sm = carve_eval(p, sp, kp.tw);
+  const int kd = sp.kd;
+  float2* vz = reinterpret_cast<float2*>(p);
+  float2 *zc = vz, *z1 = vz + kd, *zL = vz + 2 * kd, *zR = vz + 3 * kd, *sz = vz + 4 * kd;
+  float* vf = reinterpret_cast<float*>(vz + 5 * kd);
+  float *g1 = vf, *p1 = vf + kd, *pL = vf + 2 * kd, *pR = vf + 3 * kd, *gL = vf + 4 * kd;
+  float *gR = vf + 5 * kd, *rho = vf + 6 * kd, *srho = vf + 7 * kd;
+  float* p1n = vf + 8 * kd;                        // next momentum (swapped with p1 per leaf)
+  float* ckp = vf + 9 * kd;                        // [(depth+1)][kd]
+  float* ckr = ckp + (size_t)(sp.depth + 1) * kd;
+  float* uleaf = ckr + (size_t)(sp.depth + 1) * kd;   // leaf uniforms of the current subtree
+  const double beta = kp.beta[prob];
+  const DF beta_df = to_df(beta);
+  const float eps_f = (float)kp.eps[prob];
+  if (tid < 4) s_minv[tid] = (float)kp.minv[4 * prob + tid];
+  const float* minv = s_minv;
+  const double* zg = kp.z + gi * (int64_t)kd;
+  init_block_tables(sm);
+  for (int i = tid; i < n; i += blockDim.x) {
+    const DF v = to_df(zg[i]);
+    zc[i] = make_float2(v.hi, v.lo);
+    z1[i] = zc[i];
+  }
+  if (tid < kp.max_depth) {   // direction (u01 < 1/2 <=> top bit clear) and top uniform per depth
+    const Rand4 w = draw(kp.seed, pkey, li, stage, round, PU_DIRECTION, (uint64_t)tid);
+    s_dir[tid] = (w.w[0] >> 63) ? 1 : -1;
+    const Rand4 t = draw(kp.seed, pkey, li, stage, round, PU_TOP, (uint64_t)tid);
+    s_utop[tid] = u01f(t.w[0]);
+  }
+  __syncthreads();
+  unsigned long long cs_done = 0;   // component*samples computed (thread 0)
+  // one evaluation call site: iteration l = -1 evaluates the initial point, then the leaves
+  // l = 0 .. 2^depth - 1 of each subtree follow in order (see k_nuts for the flags)
+  int depth = 0, l = -1;
+  float de_c = 0.f;
+  bool moved = false;   // the transition's point changed (read by warp 0)
+  for (;;) {
+    const int nsub = 1 << depth;
+    if (l == 0) {   // a new subtree: its leaves' uniforms, and the end it grows from
+      for (int q = tid + 1; q < nsub; q += blockDim.x) {
+        const Rand4 w = draw(kp.seed, pkey, li, stage, round, PU_LEAF, (uint64_t)((nsub - 1) + q));
+        uleaf[q] = u01f(w.w[0]);
+      }
+      const int dir = s_dir[depth];
+      if (warp == 0) {
+        if (lane == 0) {
+          s_ctl[5] = DF{-INFINITY, 0.f};
+          s_flag[0] = 1;
+        }
+        const float2* zs0 = dir > 0 ? zR : zL;
+        const float *ps0 = dir > 0 ? pR : pL, *gs0 = dir > 0 ? gR : gL;
+        for (int i = lane; i < n; i += 32) {
+          z1[i] = zs0[i]; p1[i] = ps0[i]; g1[i] = gs0[i]; srho[i] = 0.f;
+        }
+      }
+      __syncthreads();
+      de_c = dir > 0 ? eps_f : -eps_f;
+    }
+    {
+      // leapfrog (l >= 0): half step in momentum and full step in position, element by
+      // element inside the evaluation's setup
+      const LeapPre<float2> leap{p1, g1, z1, minv, de_c};
+      block_eval_mixed<MODEL, R, true, false, float, false, float2>(
+          pb, kp.pa, K, beta, z1, sm, g1, nullptr, l >= 0 ? &leap : nullptr, beta_df);
+    }
+    if (tid == 0) cs_done += (unsigned long long)*sm.scalc();
+    const float* f = sm.scalf();
+    const DF logp{f[0], f[1]};
+    if (l < 0) {   // initial point: momentum, H0 and both trajectory ends
+      if (warp == 0) {
+        for (int i = lane; i < n; i += 32) {
+          const float pm = sqrtf(1.0f / minv[i % D]) *
+                           momentum_normal_f(kp.seed, pkey, li, stage, round, (uint64_t)i);
+          pL[i] = pm; pR[i] = pm; rho[i] = pm;
+          zL[i] = zc[i]; zR[i] = zc[i];
+          gL[i] = g1[i]; gR[i] = g1[i];
+        }
+        __syncwarp();
+        float kin = 0.f;
+        for (int i = lane; i < n; i += 32) kin += minv[i % D] * pL[i] * pL[i];
+        kin = warp_sum(kin);
+        if (lane == 0) {
+          const DF H0 = df_add_f(df_neg(logp), 0.5f * kin);
+          s_ctl[0] = H0;
+          s_ctl[1] = df_neg(H0);
+          s_acc = 0.f;
+          s_ctl[3] = DF{f[2], f[3]};
+          s_ctl[4] = DF{f[4], f[5]};
+          s_flag[3] = 0; s_flag[4] = 0; s_flag[5] = 0;
+        }
+      }
+      if (kp.max_depth <= 0) break;
+      l = 0;
+      continue;
+    }
+    // ---- leaf: warp 0 energy and multinomial choice; warp uw momentum, checkpoints and
+    // U-turn checks of the subtrees the leaf closes (as in k_nuts) ----
+    const int uw = blockDim.x > 32 ? 1 : 0;
+    if (warp == 0) {
+      float kin = 0.f;
+      for (int i = lane; i < n; i += 32) {
+        const float pn = p1[i] + 0.5f * de_c * g1[i];
+        kin += minv[i % D] * pn * pn;
+      }
+      kin = warp_sum(kin);
+      const DF H = df_add_f(df_neg(logp), 0.5f * kin);
+      int ok = 1, take = 0;
+      if (lane == 0) {
+        s_flag[3] += 1;
+        const bool fin = isfinite(H.hi) && isfinite(H.lo);
+        const float dH = fin ? df_sub_f(H, s_ctl[0]) : INFINITY;   // H - H0
+        if (fin) {
+          const float a = expf(-dH);
+          s_acc += a < 1.0f ? a : 1.0f;
+        }
+        if (!fin || dH > 1000.0f) {
+          ok = 0;
+          s_flag[4] = 1;
+        } else {
+          const DF lw = df_neg(H);
+          const DF nl = df_lae(s_ctl[5], lw);
+          take = (l == 0);
+          if (!take) take = uleaf[l] < expf(df_sub_f(lw, nl));
+          if (take) { s_ctl[6] = DF{f[2], f[3]}; s_ctl[7] = DF{f[4], f[5]}; }
+          s_ctl[5] = nl;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      take = __shfl_sync(0xffffffffu, take, 0);
+      if (ok && take)
+        for (int i = lane; i < n; i += 32) sz[i] = z1[i];
+      if (lane == 0) s_flag[0] = ok;
+    }
+    if (warp == uw) {
+      for (int i = lane; i < n; i += 32) p1n[i] = p1[i] + 0.5f * de_c * g1[i];
+      for (int mm = 1; mm <= depth; ++mm) {
+        if ((l & ((1 << mm) - 1)) == 0) {
+          for (int i = lane; i < n; i += 32) {
+            ckp[mm * kd + i] = p1n[i];
+            ckr[mm * kd + i] = srho[i];
+          }
+        }
+      }
+      for (int i = lane; i < n; i += 32) srho[i] += p1n[i];
+      __syncwarp();
+      int uok = 1;
+      for (int mm = 1; mm <= depth && uok; ++mm) {
+        if (((l + 1) & ((1 << mm) - 1)) == 0) {
+          float s1 = 0.f, s2 = 0.f;
+          for (int i = lane; i < n; i += 32) {
+            const float seg = srho[i] - ckr[mm * kd + i];
+            const float mi = minv[i % D];
+            s1 += seg * (mi * ckp[mm * kd + i]);
+            s2 += seg * (mi * p1n[i]);
+          }
+          s1 = warp_sum(s1);
+          s2 = warp_sum(s2);
+          if (s1 <= 0.f || s2 <= 0.f) uok = 0;
+        }
+      }
+      if (lane == 0) s_flag[6] = uok;
+    }
+    __syncthreads();
+    {
+      float* t = p1; p1 = p1n; p1n = t;   // p1 now holds p'
+    }
+    if (s_flag[0] == 0 || s_flag[6] == 0) break;   // divergence or a U-turn inside the subtree
+    if (++l < nsub) continue;
+    // ---- subtree complete: merge it into the trajectory ----
+    if (warp == 0) {
+      const int dir = s_dir[depth];
+      float2* ze = dir > 0 ? zR : zL;
+      float *pe = dir > 0 ? pR : pL, *ge = dir > 0 ? gR : gL;
+      for (int i = lane; i < n; i += 32) { ze[i] = z1[i]; pe[i] = p1[i]; ge[i] = g1[i]; }
+      int take = 0;
+      if (lane == 0) {
+        take = s_utop[depth] < expf(df_sub_f(s_ctl[5], s_ctl[1]));
+        if (take) { s_ctl[3] = s_ctl[6]; s_ctl[4] = s_ctl[7]; }
+        s_ctl[1] = df_lae(s_ctl[1], s_ctl[5]);
+        s_flag[5] = depth + 1;
+      }
+      take = __shfl_sync(0xffffffffu, take, 0);
+      if (take) {
+        moved = true;
+        for (int i = lane; i < n; i += 32) zc[i] = sz[i];
+      }
+      for (int i = lane; i < n; i += 32) rho[i] += srho[i];
+      __syncwarp();
+      const float dl = warp_dot_minv<float>(rho, pL, minv, n, D);
+      const float dr = warp_dot_minv<float>(rho, pR, minv, n, D);
+      if (lane == 0) s_flag[1] = (dl <= 0.f || dr <= 0.f) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_flag[1]) break;            // U-turn of the whole trajectory
+    if (++depth >= kp.max_depth) break;
+    l = 0;
+  }
+  if (warp == 0) {
+    if (moved) {   // an unmoved particle keeps its FP64 coordinates exactly
+      double* zw = kp.z + gi * (int64_t)kd;
+      for (int i = lane; i < n; i += 32) zw[i] = to_double(zc[i]);
+    }
+    if (lane == 0) {
+      const int leaves = s_flag[3];
+      kp.ll_old[gi] = df_to_double(s_ctl[3]);
+      kp.ll_new[gi] = df_to_double(s_ctl[4]);
+      if (out.acc) out.acc[gi] = leaves > 0 ? (double)s_acc / leaves : 0.0;
+      if (out.nleaf) out.nleaf[gi] = leaves;
+      if (out.flags) out.flags[gi] = s_flag[4] | (s_flag[5] << 8);
+      if (kp.cs_count) {  // slots 1 / 3: NUTS (initial point + every leaf), nominal / computed
+        atomicAdd(kp.cs_count + 1, (unsigned long long)n / D * (unsigned long long)pb.n *
+                                       (unsigned long long)(leaves + 1));
+        atomicAdd(kp.cs_count + 3, cs_done);
       }
     }
   }
@@ -998,21 +1288,29 @@ __global__ void __launch_bounds__(1024) k_temper_mixed(TemperIO io, int P, float
 }
 
 // ---------------------------------------------------------------------------
-// Systematic resampling (the resampling step of Sec. 2; one block per problem): FP64
-// inclusive scan of
-// W_i = exp(logw_i - max), U from Philox, a_i = min{j : C_j > (i+U)/P C_P}.
+// Systematic resampling (the resampling step of Sec. 2; one block per problem) on
+// quantised weights: W_i = round(exp(logw_i - max) 2^S), S = 52 - ceil(log2 P), so the
+// inclusive prefix sums C_j are exact integers (at most 2^52) whatever the summation
+// order, and a_i = min{j : C_j > t_i}, t_i = min((i + U) / P C_P, C_P - 1), U from Philox.
+// The ancestors are therefore the same bit for bit on any summation schedule.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_resample(const double* logw_all, double* cw_all,
+__host__ __device__ __forceinline__ int resample_scale(int P) {
+  int S = 52;
+  for (long long q = 1; q < (long long)P; q <<= 1) --S;
+  return S;
+}
+
+__global__ void __launch_bounds__(1024) k_resample(const double* logw_all, long long* cw_all,
                                                    int32_t* anc_all, const ProbDev* probs,
                                                    uint64_t seed, int stage, int P,
                                                    int prob_base) {
-  __shared__ double red[128];
-  __shared__ double s_carry[33];
+  __shared__ double red[32];
+  __shared__ long long s_carry[33];
   __shared__ double s_m;
   const int prob = blockIdx.x;
   if (probs[prob].done) return;
   const double* logw = logw_all + (int64_t)prob * P;
-  double* C = cw_all + (int64_t)prob * P;
+  long long* C = cw_all + (int64_t)prob * P;
   int32_t* anc = anc_all + (int64_t)prob * P;
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double mx = -INFINITY;
@@ -1027,40 +1325,45 @@ __global__ void __launch_bounds__(1024) k_resample(const double* logw_all, doubl
   }
   __syncthreads();
   const double m = s_m;
+  const double scale = ldexp(1.0, resample_scale(P));   // exact power of two
   // contiguous chunk per thread, sequential local scan, then block exclusive scan
   const int chunk = (P + T - 1) / T;
   const int b = tid * chunk, e = min(P, b + chunk);
-  double run = 0.0;
-  for (int i = b; i < e; ++i) { run += exp(logw[i] - m); C[i] = run; }
-  // exclusive scan of per-thread totals across the block
-  double x = run;
+  long long run = 0;
+  for (int i = b; i < e; ++i) {
+    const double w = exp(__dadd_rn(logw[i], -m));
+    run += w > 0.0 ? __double2ll_rn(__dmul_rn(w, scale)) : 0ll;   // NaN, 0: no weight
+    C[i] = run;
+  }
+  long long x = run;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  double excl = __shfl_up_sync(0xffffffffu, x, 1);
-  if (lane == 0) excl = 0.0;
+  long long excl = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) excl = 0;
   if (lane == 31) s_carry[warp] = x;
   __syncthreads();
   if (tid == 0) {
-    double c = 0.0;
-    for (int w = 0; w < (T >> 5); ++w) { const double t = s_carry[w]; s_carry[w] = c; c += t; }
+    long long c = 0;
+    for (int w = 0; w < (T >> 5); ++w) { const long long t = s_carry[w]; s_carry[w] = c; c += t; }
     s_carry[32] = c;
   }
   __syncthreads();
-  const double off = s_carry[warp] + excl;
+  const long long off = s_carry[warp] + excl;
   for (int i = b; i < e; ++i) C[i] += off;
   __syncthreads();
-  const double total = C[P - 1];
+  const double total = (double)C[P - 1];       // exact: at most 2^52
   const Rand4 w = draw(seed, prob + prob_base, 0, stage, 0, PU_RESAMPLE, 0);
   const double U = u01(w.w[0]);
   for (int i = tid; i < P; i += T) {
-    const double target = ((double)i + U) / (double)P * total;
+    double target = __dmul_rn(__ddiv_rn(__dadd_rn((double)i, U), (double)P), total);
+    if (target > total - 1.0) target = total - 1.0;
     int lo = 0, hi = P - 1;    // first j with C_j > target (C_{P-1} = total > target)
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (C[mid] > target) hi = mid; else lo = mid + 1;
+      if ((double)C[mid] > target) hi = mid; else lo = mid + 1;
     }
     anc[i] = lo;
   }

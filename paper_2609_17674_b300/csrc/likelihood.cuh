@@ -305,7 +305,8 @@ __device__ __forceinline__ void mixed_sub(const float (&cf)[C][NCF], float m, fl
 
 // adjoint partial sums of C components over the thread's samples
 // (rc = c_n r_n / sigma^2, packed pairs as above); C as in mixed_sub
-//   pulse:    s0 = sum rc g, s1 = sum rc g v, s2 = sum rc g v^2
+//   pulse:    s0 = sum rc g, s1 = sum rc g v, s2 = sum rc g v^2 (per 8-sample chunk from
+//             running sums, combined with the chunk's end point)
 //   sinusoid: s0 = sum rc cos, s1 = sum rc sin, s2 = sum rc sin n, s3 = sum rc sin n^2
 template <int MODEL, int R, int C>
 __device__ __forceinline__ void mixed_adj(const float (&cf)[C][NCF], float m,
@@ -367,37 +368,48 @@ __device__ __forceinline__ void mixed_adj(const float (&cf)[C][NCF], float m,
       o[0][0] = a0.x + a0.y; o[0][1] = a1.x + a1.y; o[0][2] = a2.x + a2.y; o[0][3] = 0.f;
       return;
     }
+    const float2 ndel = f2(-cf[0][3]), ndel2 = f2(-2.0f * cf[0][3]), del2 = f2(cf[0][7]);
 #pragma unroll
     for (int p = 0; p < R / 16; ++p) {
-      float2 v0[C], g[C], q[C], a0[C], a1[C], a2[C];
+      float2 v0[C], g[C], q[C], c[C], e[C], fs[C];
 #pragma unroll
       for (int u = 0; u < C; ++u) {
         v0[u] = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del[u], v00[u]);
         g[u] = make_float2(ex2a(-v0[u].x * v0[u].x), ex2a(-v0[u].y * v0[u].y));
         q[u] = make_float2(ex2a(fminf(-__fmaf_rn(v0[u].x, cf[u][6], cf[u][7]), 64.0f)),
                            ex2a(fminf(-__fmaf_rn(v0[u].y, cf[u][6], cf[u][7]), 64.0f)));
-        a0[u] = a1[u] = a2[u] = f2(0.f);
       }
+      // running sums over the chunk with p_j = rc_j g_j: c_k = sum_{j<=k} p_j,
+      // e_k = sum_{m<=k} c_m, f_k = sum_{m<=k} e_m, so that at its end c = sum p,
+      // e = sum (8 - j) p and f = sum (8 - j)(9 - j)/2 p (five packed operations per step
+      // and no per-step constants)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
 #pragma unroll
         for (int u = 0; u < C; ++u) {
-          const float2 pr = __fmul2_rn(rc[8 * p + j], g[u]);
-          a0[u] = __fadd2_rn(a0[u], pr);
-          a1[u] = __ffma2_rn(pr, f2((float)j), a1[u]);
-          a2[u] = __ffma2_rn(pr, f2((float)(j * j)), a2[u]);
+          if (j == 0) {
+            c[u] = __fmul2_rn(rc[8 * p], g[u]);
+            e[u] = c[u];
+            fs[u] = c[u];
+          } else {
+            c[u] = __ffma2_rn(rc[8 * p + j], g[u], c[u]);
+            e[u] = __fadd2_rn(e[u], c[u]);
+            fs[u] = __fadd2_rn(fs[u], e[u]);
+          }
           g[u] = __fmul2_rn(g[u], q[u]);
           q[u] = __fmul2_rn(q[u], rho[u]);
         }
       }
 #pragma unroll
       for (int u = 0; u < C; ++u) {
-        // per chunk: sum p v = v0 a0 + del a1;  sum p v^2 = v0^2 a0 + 2 v0 del a1 + del^2 a2
-        const float2 c1 = __ffma2_rn(v0[u], a0[u], __fmul2_rn(del[u], a1[u]));
-        const float2 c2 = __ffma2_rn(v0[u], __ffma2_rn(v0[u], a0[u],
-                                                       __fmul2_rn(f2(2.0f * cf[u][3]), a1[u])),
-                                     __fmul2_rn(f2(cf[u][7]), a2[u]));
-        s0[u] += a0[u].x; s0[u] += a0[u].y;            // chunks in sample order
+        // with w = 8 - j and V = v0 + 8 del (v one past the chunk): v = V - del w, so
+        // sum p v = V c - del e;  sum p v^2 = V^2 c - 2 V del e + del^2 (2 f - e)
+        const float2 V = __ffma2_rn(f2(8.0f), del[u], v0[u]);
+        const float2 c1 = __ffma2_rn(V, c[u], __fmul2_rn(ndel, e[u]));
+        const float2 w2 = __ffma2_rn(f2(2.0f), fs[u], make_float2(-e[u].x, -e[u].y));
+        const float2 c2 = __ffma2_rn(V, __ffma2_rn(V, c[u], __fmul2_rn(ndel2, e[u])),
+                                     __fmul2_rn(del2, w2));
+        s0[u] += c[u].x; s0[u] += c[u].y;            // chunks in sample order
         s1[u] += c1.x; s1[u] += c1.y;
         s2[u] += c2.x; s2[u] += c2.y;
       }
@@ -504,7 +516,7 @@ struct EvalSmem {
   double* wacc;   // [nwarps][KDmax] per-warp gradient slot sums
   double* wfis;   // [nwarps][KDmax] per-warp Gauss-Newton slot sums
   double* red;    // [32*4] reduction scratch
-  double* scal;   // [4]: logp, ll_old, ll_new, component*samples computed
+  double* scal;   // [8]: logp, ll_old, ll_new, component*samples computed; [4..7] see scalf
   const double* tw;  // LINAMP fixed (t0, w) [kmax][2] (global)
   float2* exptab;    // mixed path: 2^(j/64), j < 64, as double-float (filled per block)
   // mixed path: FP32 views of the same storage
@@ -514,6 +526,10 @@ struct EvalSmem {
   __device__ float* fpc() const { return reinterpret_cast<float*>(pc); }
   __device__ float2* wacc2() const { return reinterpret_cast<float2*>(wacc); }
   __device__ float2* wfis2() const { return reinterpret_cast<float2*>(wfis); }
+  // double-float totals of the mixed NUTS evaluation (scal[4..7]): logp, ll_old, ll_new as
+  // hi/lo pairs, then the component*samples computed as an int
+  __device__ float* scalf() const { return reinterpret_cast<float*>(scal + 4); }
+  __device__ int* scalc() const { return reinterpret_cast<int*>(scal + 4) + 6; }
 };
 
 // ---------------------------------------------------------------------------
@@ -631,19 +647,20 @@ __device__ __forceinline__ DF df_exp(DF x, const float2* tab) {
 // map), with s(z) and 1 - s(z) both from e^{-|z|}; also returns dtheta/dz in FP32
 struct Coord32 { float th, dth, lp, pg, pc; };
 
-// theta in double-float; with pr != nullptr also the log prior density of z and its
-// first two derivatives (lp, pg, pc of Coord32) from the same e^{-|z|} and 1/(1+e)
-__device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, double z, const float2* tab,
+// theta in double-float from a double-float coordinate z; with pr != nullptr also the log
+// prior density of z and its first two derivatives (lp, pg, pc of Coord32) from the same
+// e^{-|z|} and 1/(1+e)
+__device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, DF z, const float2* tab,
                                        float& dth, Coord32* pr = nullptr) {
-  const float zh = (float)z;
-  const DF az = zh >= 0.f ? DF{zh, (float)(z - (double)zh)} : DF{-zh, -(float)(z - (double)zh)};
+  const bool pos = z.hi >= 0.f;
+  const DF az = pos ? z : df_neg(z);
   const DF e = df_exp(df_neg(az), tab);              // e^{-|z|}
   const DF q = df_recip(df_add(DF{1.0f, 0.0f}, e));  // 1 / (1 + e)
   const DF eq = df_mul(e, q);
-  const DF s = z >= 0.0 ? q : eq;                    // s(z)
+  const DF s = pos ? q : eq;                         // s(z)
   const float ds = __fmul_rn(q.hi, eq.hi);           // s (1 - s)
   if (pr) {
-    const float sc = z >= 0.0 ? eq.hi : q.hi;        // 1 - s
+    const float sc = pos ? eq.hi : q.hi;             // 1 - s
     pr->lp = -az.hi - 2.f * log1pf(e.hi);
     pr->pg = sc - s.hi;
     pr->pc = 2.f * ds;
@@ -1078,38 +1095,66 @@ __device__ void block_eval_fp64(const ProbDev& pb, const PriorArgs& pa, int K, d
 // only for the sinusoid frequency map and phase constants and the final scalars.
 // The serial parts run one thread per (component, parameter) where they can.
 // ---------------------------------------------------------------------------
+// Particle coordinates as FP64 (caller arrays) or double-float pairs (the mixed NUTS
+// kernel's positions, updated without FP64 instructions)
+__device__ __forceinline__ DF to_df(double z) {   // beyond the FP32 range: (+-inf, 0)
+  const float h = (float)z;
+  return DF{h, isfinite(h) ? (float)(z - (double)h) : 0.f};
+}
+__device__ __forceinline__ DF to_df(float2 z) { return DF{z.x, z.y}; }
+__device__ __forceinline__ double to_double(double z) { return z; }
+__device__ __forceinline__ double to_double(float2 z) { return (double)z.x + (double)z.y; }
+// z += step, the leapfrog position step
+__device__ __forceinline__ void pos_add(double& z, float step) { z = z + (double)step; }
+__device__ __forceinline__ void pos_add(float2& z, float step) {
+  if (!isfinite(z.x)) {   // a coordinate beyond the FP32 range stays where it is
+    z.x += step;
+    return;
+  }
+  const DF s = two_sum(z.x, step);
+  const DF r = quick_two_sum(s.hi, __fadd_rn(s.lo, z.y));
+  z = make_float2(r.hi, r.lo);
+}
+
 // Leapfrog step folded into the mixed setup (NUTS): element i's thread applies the
 // momentum half step p_i += eps/2 g_i and the position step z_i += eps minv p_i before it
-// maps z_i, with the arithmetic of the separate update (FP32 control, FP64 positions).
+// maps z_i, with the arithmetic of the separate update (FP32 control; positions FP64 or
+// double-float).
+template <typename ZT>
 struct LeapPre {
   float* p1;
   const float* g1;
-  double* z1;
+  ZT* z1;
   const float* minv;
   float de_c;
 };
 
-template <int MODEL, int R>
-__device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const double* z,
-                                  EvalSmem& sm, const LeapPre* leap = nullptr) {
+template <int MODEL, int R, typename ZT>
+__device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const ZT* z,
+                                  EvalSmem& sm, const LeapPre<ZT>* leap = nullptr) {
   constexpr int D = model_d<MODEL>();
   float lp = 0.f;
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
   const int KD = K * D;
   float* th_lo = th + KD;       // double-float low parts of the pulse centre and width
-  // (1) one thread per (component, parameter): coordinate map, Jacobian, prior terms
-  for (int i = threadIdx.x; i < KD; i += blockDim.x) {
-    const int d = i % D;
+  // (1) one thread per (component, parameter), parameter-major over a component count
+  // padded to 32 so that every warp maps one parameter (no divergence between the
+  // maps of different parameters): element e -> d = e / Kw, k = e % Kw
+  const int Kw = (K + 31) & ~31;
+  for (int e = threadIdx.x; e < D * Kw; e += blockDim.x) {
+    const int d = e / Kw, k = e - d * Kw;
+    if (k >= K) continue;
+    const int i = k * D + d;
     if (leap) {
       const float ph = leap->p1[i] + 0.5f * leap->de_c * leap->g1[i];
       leap->p1[i] = ph;
-      leap->z1[i] = leap->z1[i] + (double)(leap->de_c * leap->minv[d] * ph);
+      pos_add(leap->z1[i], leap->de_c * leap->minv[d] * ph);
     }
-    const double zi = z[i];
+    const ZT zi = z[i];
     if (MODEL == PULSE && d > 0) {
       // centre and width to ~1e-12 relative in double-float (FP32 pipe, no FP64)
       Coord32 c;
-      const DF t = theta_df(pb, d, zi, sm.exptab, c.dth, &c);
+      const DF t = theta_df(pb, d, to_df(zi), sm.exptab, c.dth, &c);
       th[i] = t.hi;
       th_lo[i] = t.lo;
       dth[i] = c.dth;
@@ -1117,7 +1162,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       pcv[i] = c.pc;
       lp += c.lp;
     } else {
-      const Coord32 c = coord32(pb, pa, d, (float)zi);
+      const Coord32 c = coord32(pb, pa, d, to_df(zi).hi);
       th[i] = c.th;
       dth[i] = c.dth;
       pgv[i] = c.pg;
@@ -1125,7 +1170,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       lp += c.lp;
       if (MODEL == SINUSOID && d == 1) {   // frequency in FP64 for the phase constants
         double d1;
-        sm.wacc[i / D] = theta64(pb, 1, zi, d1);   // scratch until the sample loop
+        sm.wacc[i / D] = theta64(pb, 1, to_double(zi), d1);   // scratch until the sample loop
         dth[i] = (float)d1;
       }
     }
@@ -1154,14 +1199,19 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   return lp;
 }
 
-template <int MODEL, int R, bool GRAD, bool FISHER, typename GT>
+// F64OUT: FP64 totals into sm.scal (logp, ll_old, ll_new, count); otherwise double-float
+// totals into sm.scalf() (logp, ll_old, ll_new as hi/lo pairs) and the count into
+// sm.scalc(), with no FP64 instruction (the mixed NUTS kernel).  beta_df: beta as
+// double-float (used when !F64OUT).
+template <int MODEL, int R, bool GRAD, bool FISHER, typename GT, bool F64OUT = true,
+          typename ZT = double>
 __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, double beta,
-                                 const double* z, EvalSmem& sm, GT* grad_out, double* fis_out,
-                                 const LeapPre* leap = nullptr) {
+                                 const ZT* z, EvalSmem& sm, GT* grad_out, double* fis_out,
+                                 const LeapPre<ZT>* leap = nullptr, DF beta_df = DF{0.f, 0.f}) {
   constexpr int D = model_d<MODEL>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nw = blockDim.x >> 5;
-  const float lp_t = eval_setup_mixed<MODEL, R>(pb, pa, K, z, sm, leap);
+  const float lp_t = eval_setup_mixed<MODEL, R, ZT>(pb, pa, K, z, sm, leap);
 
   // sample indices fit 32 bits (capacity < 2^24): no 64-bit integer work or
   // 64-bit conversions (which issue on the FP64 pipe) inside the sample loop
@@ -1427,13 +1477,24 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
       cp += rf[w * 6 + 4];
       cnt += ri[w];
     }
-    const double lo = -0.5 * df_to_double(a) * pb.inv_s2;
-    const double ln = -0.5 * df_to_double(b) * pb.inv_s2;
-    const double lp = isfinite(cp) ? df_to_double(c) : (double)cp;
-    sm.scal[0] = lo + beta * ln + lp;
-    sm.scal[1] = lo;
-    sm.scal[2] = ln;
-    sm.scal[3] = (double)cnt;
+    if constexpr (F64OUT) {
+      const double lo = -0.5 * df_to_double(a) * pb.inv_s2;
+      const double ln = -0.5 * df_to_double(b) * pb.inv_s2;
+      const double lp = isfinite(cp) ? df_to_double(c) : (double)cp;
+      sm.scal[0] = lo + beta * ln + lp;
+      sm.scal[1] = lo;
+      sm.scal[2] = ln;
+      sm.scal[3] = (double)cnt;
+    } else {
+      const DF nis{-0.5f * pb.f_is2.x, -0.5f * pb.f_is2.y};   // -1/(2 sigma^2), exact halving
+      const DF lo = df_mul(a, nis), ln = df_mul(b, nis);
+      DF lg = df_add(lo, df_mul(beta_df, ln));
+      if (isfinite(cp) && isfinite(lg.hi)) lg = df_add(lg, c);
+      else lg = DF{lg.hi + cp, 0.f};   // -inf log prior, or a NaN likelihood
+      float* f = sm.scalf();
+      f[0] = lg.hi; f[1] = lg.lo; f[2] = lo.hi; f[3] = lo.lo; f[4] = ln.hi; f[5] = ln.lo;
+      *sm.scalc() = (int)cnt;
+    }
   }
   __syncthreads();
 }
@@ -1442,7 +1503,7 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
 template <int MODEL, int PREC>
 __device__ __forceinline__ double eval_setup(const ProbDev& pb, const PriorArgs& pa, int K,
                                              const double* z, EvalSmem& sm) {
-  if constexpr (PREC == MIXED) return (double)eval_setup_mixed<MODEL, 32>(pb, pa, K, z, sm);
+  if constexpr (PREC == MIXED) return (double)eval_setup_mixed<MODEL, 32, double>(pb, pa, K, z, sm);
   else return eval_setup_any<MODEL, PREC>(pb, pa, K, z, sm);
 }
 
@@ -1450,10 +1511,9 @@ __device__ __forceinline__ double eval_setup(const ProbDev& pb, const PriorArgs&
 template <int MODEL, int PREC, int R, bool GRAD, bool FISHER, typename GT = double>
 __device__ __forceinline__ void block_eval(const ProbDev& pb, const PriorArgs& pa, int K,
                                            double beta, const double* z, EvalSmem& sm,
-                                           GT* grad_out, double* fis_out,
-                                           const LeapPre* leap = nullptr) {
+                                           GT* grad_out, double* fis_out) {
   if constexpr (PREC == MIXED)
-    block_eval_mixed<MODEL, R, GRAD, FISHER, GT>(pb, pa, K, beta, z, sm, grad_out, fis_out, leap);
+    block_eval_mixed<MODEL, R, GRAD, FISHER, GT>(pb, pa, K, beta, z, sm, grad_out, fis_out);
   else
     block_eval_fp64<MODEL, PREC, R, GRAD, FISHER>(pb, pa, K, beta, z, sm, grad_out, fis_out);
 }
