@@ -267,8 +267,9 @@ def measure_extras(stream):
             se_h = np.sqrt(hs.var(0, ddof=1) / len(hs) + gh.var(0, ddof=1) / len(gh))
             se_z = math.sqrt(zs.var(ddof=1) / len(zs) + gz.var(ddof=1) / len(gz))
             res[name] = {"wall_s_per_run": float(np.median(ts)), "logz": float(zs.mean()),
-                         "within_3se": bool(np.all(np.abs(hs.mean(0) - gh.mean(0)) <= 3 * se_h + 0.01)
-                                            and abs(zs.mean() - gz.mean()) <= 3 * se_z + 0.02)}
+                         "within_3se": bool(np.all(np.abs(hs.mean(0) - gh.mean(0))
+                                                   <= np.maximum(3 * se_h, 1.0 / w1.P))
+                                            and abs(zs.mean() - gz.mean()) <= 3 * se_z)}
         res["oracle_logz"] = float(gz.mean())
         res["fp64_over_mixed_wall"] = res["fp64"]["wall_s_per_run"] / res["mixed"]["wall_s_per_run"]
         out["smc_equal_error_pulse_n1024_p512"] = res

@@ -139,10 +139,11 @@ def test_smc_with_population_births_reaches_the_oracle_posterior():
 
     hg, sg = mean_se([r["hist"] for r in runs])
     ho, so = mean_se([r["hist"] for r in gold])
-    assert np.all(np.abs(hg - ho) <= 3 * np.sqrt(sg**2 + so**2) + 0.01), (hg, ho)
+    # 3 standard errors, floored at one particle's mass (the histogram's resolution)
+    assert np.all(np.abs(hg - ho) <= np.maximum(3 * np.sqrt(sg**2 + so**2), 1.0 / 512)), (hg, ho)
     lg, slg = mean_se([r["logz"] for r in runs])
     lo, slo = mean_se([r["logz"] for r in gold])
-    assert abs(lg - lo) <= 3 * math.hypot(slg, slo) + 0.02, (lg, lo)
+    assert abs(lg - lo) <= 3 * math.hypot(slg, slo), (lg, lo)
     for key in ("t0_sorted_mean", "A_by_t0_mean"):
         xg = [r[key] for r in runs if key in r]
         xo = [r[key] for r in gold if key in r]
