@@ -70,8 +70,7 @@ typedef struct {
   double amp_mean, amp_sd;          /* LINAMP Gaussian amplitude prior */
   uint64_t seed;          /* Philox4x64-10 key word 0 (word 1 = problem_base + problem index) */
   int32_t threads;        /* threads per particle block (32..256, multiple of 32); 0: default
-                             (on TSMC_MIXED 256 for TSMC_SINUSOID, 96 for TSMC_PULSE; else
-                             128) */
+                             (64 for TSMC_PULSE on TSMC_MIXED; else 128) */
   int32_t samples_per_thread;  /* mixed path register tile: 0 (default 32), 16 or 32 */
   int32_t pulse_window;   /* mixed pulse path: 1 skips every (component, 32-thread sample
                              range) pair where |t - t0| > 6 w throughout, i.e. all template

@@ -544,14 +544,13 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->D = model_dim(cfg->model);
   c->kd = cfg->kmax * c->D;
   c->Ptot = (int64_t)cfg->n_problems * cfg->particles;
-  // default block: 128 threads; on the mixed path 256 for sinusoids (their rotation
-  // recurrence is latency-bound and gains from the extra warps per block) and 96 for pulses
-  // (five resident blocks of three warps: fewer warps idle while one runs a block's serial
-  // work)
+  // default block: 128 threads; on the mixed path 64 for pulses (eight resident two-warp
+  // blocks per SM at 26 KB of shared memory and <= 128 registers: more particles in flight
+  // while one block runs its serial per-leaf work, and the 16 warp ranges of 1024 samples
+  // of N = 16384 split evenly; five 96-thread blocks ran the NUTS rounds 6% slower)
   c->T = cfg->threads ? cfg->threads
          : cfg->precision != TSMC_MIXED ? 128
-         : cfg->model == TSMC_SINUSOID ? 256
-         : cfg->model == TSMC_PULSE ? 96 : 128;
+         : cfg->model == TSMC_PULSE ? 64 : 128;
   c->R = cfg->samples_per_thread ? cfg->samples_per_thread : 32;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   Layout L;

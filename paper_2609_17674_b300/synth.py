@@ -122,8 +122,10 @@ def gb_amp_bounds(n, dt, sigma, f_c):
     return 5.0 * sigma / norm, 60.0 * sigma / norm
 
 
-def sinusoid_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F_HI) -> Problem:
-    """Quasi-monochromatic sinusoids with per-source SNR ~ U[10, 40] (time-domain rho)."""
+def sinusoid_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F_HI,
+                     noise=True) -> Problem:
+    """Quasi-monochromatic sinusoids with per-source SNR ~ U[10, 40] (time-domain rho); white
+    noise of level sigma unless noise=False (the paper's example data are noise-free)."""
     t = np.arange(n, dtype=np.float64) * dt
     f = f_lo + (f_hi - f_lo) * rng.random(k_true)
     fd = GB_FDOT_HI * rng.random(k_true)
@@ -135,7 +137,9 @@ def sinusoid_problem(rng, n, k_true, dt=15.0, sigma=1.0, f_lo=GB_F_LO, f_hi=GB_F
         c = np.cos(_sin_phase(t, f[k], fd[k], p0[k]))
         A[k] = rho[k] * sigma / math.sqrt(float(np.sum(c * c)))
         d += A[k] * c
-    d = d + sigma * rng.standard_normal(n)
+    noise_draw = rng.standard_normal(n)   # drawn either way: the stream is the same
+    if noise:
+        d = d + sigma * noise_draw
     a_lo, a_hi = gb_amp_bounds(n, dt, sigma, 0.5 * (f_lo + f_hi))
     truth = np.stack([A, f, fd, p0], axis=1)
     return Problem(d=d, t_origin=0.0, dt=dt, sigma=sigma, truth=truth,
@@ -189,9 +193,9 @@ def pulse_workload(name, n, k_true, kmax, P, seed, sigma=0.1, n_problems=1, **kw
                     hi=PULSE_HI, logmask=PULSE_LOGMASK, seed=seed, **kw)
 
 
-def sinusoid_workload(name, n, k_true, kmax, P, seed, **kw) -> Workload:
+def sinusoid_workload(name, n, k_true, kmax, P, seed, noise=True, **kw) -> Workload:
     rng = _rng(seed)
-    pr = sinusoid_problem(rng, n, k_true)
+    pr = sinusoid_problem(rng, n, k_true, noise=noise)
     return Workload(name=name, model=SINUSOID, kmax=kmax, P=P, problems=[pr], lo=pr.lo,
                     hi=pr.hi, logmask=0b0001, seed=seed, **kw)
 

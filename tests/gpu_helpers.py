@@ -65,3 +65,14 @@ def assert_eval_parity(ora, res, ll_old, ll_new, logp, grad, K, tol, D):
         # rows beyond K_p are zero
         for i, k in enumerate(K):
             assert np.all(g[i, k:] == 0.0)
+
+
+def data_scale_gscale(wl, z, K, beta, b=0):
+    """Gradient condition at the data scale: the oracle's sum of absolute terms evaluated on
+    data 2d, where a particle near the injection has residual ~d (used with noise-free data,
+    where the residual itself vanishes at the injection but FP32 template errors do not)."""
+    import copy
+
+    w2 = copy.deepcopy(wl)
+    w2.problems[b].d = 2.0 * w2.problems[b].d
+    return oracle.Oracle(w2, b).logl_grad(z, K, beta)["gscale"]

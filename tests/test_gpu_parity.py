@@ -11,8 +11,8 @@ import pytest
 
 import oracle
 from paper_2609_17674_b300 import capi, sampler, synth
-from gpu_helpers import (TOL, assert_eval_parity, context_with_population, dev_tensor,
-                         population, torch)
+from gpu_helpers import (TOL, assert_eval_parity, context_with_population, data_scale_gscale,
+                         dev_tensor, population, torch)
 
 pytestmark = pytest.mark.gpu
 
@@ -563,6 +563,33 @@ def test_full_size_pulse_sampled(prec):
     idx = np.r_[0, 1, np.random.default_rng(0).choice(np.arange(2, wl.P), 62, replace=False)]
     res = oracle.Oracle(wl).logl_grad(z[idx], K[idx], 0.25)
     assert_eval_parity(None, res, lo[idx], ln[idx], lp[idx], g[idx], K[idx], TOL[prec], 3)
+
+
+def test_mixed_sinusoid_noise_free_absolute_bound():
+    """Single-channel band on noise-free data (Sec. 5.2's example has no noise): particles
+    at the injection (tiny residual) and from the prior, |dlogL| <= 1e-5 (1/2 D + |logL|)
+    with D = sum d^2 / sigma^2 (FP32 templates err by ~eps32 of the signal), and the gradient
+    within 1e-5 of its sum of absolute terms at the residual plus that at the data scale."""
+    t = torch()
+    wl = synth.sinusoid_workload("t", 9000, 3, 5, 16, 52, noise=False)
+    clean = wl.problems[0].d
+    z, K = population(wl, 3, 16)
+    zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+    for i in range(2, 16, 2):
+        K[i] = 3
+        z[i] = 0.0
+        z[i, :3] = zt + 1e-6 * np.random.default_rng(i).standard_normal((3, 4))
+    ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 1.0)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([1.0], t.float64), grad=True)
+    t.cuda.synchronize()
+    res = oracle.Oracle(wl).logl_grad(z, K, 1.0)
+    half_D = 0.5 * float(np.sum(clean ** 2)) / wl.problems[0].sigma ** 2
+    err = np.abs(ln.cpu().numpy() - res["ll_new"])
+    assert np.all(err <= 1e-5 * (half_D + np.abs(res["ll_new"]))), (err.max(), half_D)
+    assert np.max(np.abs(res["ll_new"][2::2])) < 0.1 * half_D
+    gerr = np.abs(g.cpu().numpy() - res["grad"])
+    gs = res["gscale"] + data_scale_gscale(wl, z, K, 1.0)
+    assert np.all(gerr <= 1e-5 * gs + 1e-300), float(np.max(gerr / (gs + 1e-300)))
 
 
 @pytest.mark.parametrize("prec", [capi.MIXED])

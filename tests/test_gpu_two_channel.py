@@ -2,16 +2,16 @@
 a flat PSD, computed in the time domain; the oracle's pins tie it to the frequency-domain
 inner product) through the C ABI against the oracle: evaluation, Gauss-Newton sums,
 reversible jump, NUTS and one SMC stage, a full-size band on a sample of particles, and the
-argument checks.  The mixed-path comparisons use data with white noise: on noise-free data
-a particle at the injection has a residual near zero, against which FP32 template rounding
-(relative to the signal) is not a meaningful relative error."""
+argument checks.  The relative mixed-path comparisons use data with white noise; on the
+paper's noise-free data a particle at the injection has a residual near zero, so there the
+mixed path is held to an absolute bound scaled by the data energy."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2609_17674_b300 import capi, sampler, synth
-from gpu_helpers import (TOL, assert_eval_parity, context_with_population, dev_tensor,
-                         population, torch)
+from gpu_helpers import (TOL, assert_eval_parity, context_with_population, data_scale_gscale,
+                         dev_tensor, population, torch)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +38,35 @@ def test_eval_parity(prec, n):
     ora = oracle.Oracle(wl)
     res = ora.logl_grad(z, K, 0.37)
     assert_eval_parity(ora, res, lo, ln, lp, g, K, TOL[prec], 4)
+
+
+@pytest.mark.parametrize("jitter", [1e-3, 1e-6])
+def test_mixed_eval_noise_free_absolute_bound(jitter):
+    """The paper's data are noise-free (Sec. 5.2), so a particle at the injection has a residual
+    near zero and no relative bound on its likelihood is meaningful.  With FP32 templates each
+    residual carries an error of a few eps32 times the signal, which moves the energy by at
+    most ~2 eps32 sqrt(E D) + O(eps32^2 D) <= eps32 (E + D), D = sum d^2 / sigma^2 the data
+    energy: the mixed path is held to |dlogL| <= 1e-5 (1/2 D + |logL|) on every particle,
+    near the injection and far from it, and its gradient to 1e-5 of the sum of absolute
+    terms at the residual plus the same sum at the data scale."""
+    t = torch()
+    wl = synth.ae_workload("t", 4096, 3, 5, 24, 44, noise=False)
+    z, K = population(wl, 6, 24)
+    K[2::2] = 3
+    z, K = _near_injection(wl, z, K, jitter=jitter)
+    ctx, zd, Kd = context_with_population(wl, capi.MIXED, z, K, 0.8)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.8], t.float64), grad=True)
+    t.cuda.synchronize()
+    res = oracle.Oracle(wl).logl_grad(z, K, 0.8)
+    pr = wl.problems[0]
+    half_D = 0.5 * float(np.sum(pr.d ** 2)) / pr.sigma ** 2
+    err = np.abs(ln.cpu().numpy() - res["ll_new"])
+    assert np.all(err <= 1e-5 * (half_D + np.abs(res["ll_new"]))), (err.max(), half_D)
+    hard = [i for i in range(2, 24, 2) if K[i] == 3]          # all three sources, at the truth
+    assert len(hard) >= 4 and np.max(np.abs(res["ll_new"][hard])) < 0.1 * half_D
+    gerr = np.abs(g.cpu().numpy() - res["grad"])
+    gs = res["gscale"] + data_scale_gscale(wl, z, K, 0.8)
+    assert np.all(gerr <= 1e-5 * gs + 1e-300), float(np.max(gerr / (gs + 1e-300)))
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
