@@ -35,12 +35,13 @@ UNIT = "cs-evals/s"
 OPS_PER_CS = {0: 9.0, 1: 14.0}   # algorithmic FP32 lane-ops per component*sample (fwd+adj)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per particle of one NUTS launch, from an ncu capture of the
-# same kernel on a 1024-particle launch of this workload (profiles/k_nuts_pulse_n16384_p1024.md);
-# traffic scales with the particle count (z rows in and out; the samples stay in L2).
-# None when the kernel has changed since the capture.
-NUTS_DRAM_BYTES_PER_PARTICLE = 557.75
+# same kernel on a 1024-particle launch of this workload
+# (profiles/k_nuts_mixed_pulse_n16384_p1024.md); traffic scales with the particle count (z
+# rows in and out; the samples stay in L2).  None when the kernel has changed since the
+# capture.
+NUTS_DRAM_BYTES_PER_PARTICLE = 564.5
 NUTS_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of a 1024-particle launch, scaled per "
-                     "particle (profiles/k_nuts_pulse_n16384_p1024.md)")
+                     "particle (profiles/k_nuts_mixed_pulse_n16384_p1024.md)")
 
 
 def _args():
@@ -522,7 +523,7 @@ def run_gpu(a):
     mhz = clk.get("sm_mhz") or 2032.0
     n_sm = props.multi_processor_count
     peak = FP32_LANES_PER_SM * n_sm * mhz * 1e6 / 1e12
-    roof = {"kernel": "k_nuts<PULSE,MIXED,32>", "bound": "alu", "achieved": achieved,
+    roof = {"kernel": "k_nuts_mixed<PULSE,32>", "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "Tops/s (FP32 lane-ops, FMA=1)", "frac": achieved / peak,
             "traffic": NUTS_DRAM_BYTES_PER_PARTICLE * a.particles if NUTS_DRAM_BYTES_PER_PARTICLE
             else None,

@@ -69,7 +69,7 @@ class Config(C.Structure):
         ("pulse_window", C.c_int32), ("kmin", C.c_int32),
         ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
         ("channels", C.c_int32), ("response", C.c_double * 4),
-        ("problem_base", C.c_int32),
+        ("problem_base", C.c_int32), ("fused_rounds", C.c_int32),
     ]
 
 

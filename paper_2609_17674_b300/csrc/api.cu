@@ -45,6 +45,8 @@ struct tsmc_ctx {
   int32_t* order_hist = nullptr; // [kOrderBuckets] bucket counts / offsets (scratch)
   double* kde = nullptr;         // [n_problems][kKdeStride] population birth proposals
   int32_t* kcum = nullptr;       // [Ptot] prefix counts of K (scratch of the proposal build)
+  unsigned int* next = nullptr;  // work counter of the persistent mutation launch
+  int mut_grid = 0;              // resident blocks of the persistent mutation kernel
   double nmax = 1.0;             // largest problem capacity (cost normalisation)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -96,7 +98,7 @@ struct Layout {
 struct Offsets {
   size_t probs, d64, d32, z, z2, K, K2, llo, llo2, lln, lln2, logw, cw, anc, acc, nleaf, flags,
       outcome, fis, beta, logz, ess, eps, minv, stats, stage, tw, cs, order, order_hist, kde,
-      kcum;
+      kcum, next;
 };
 
 tsmc_status check_cfg(const tsmc_config* cfg) {
@@ -116,6 +118,7 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->channels < 0 || cfg->channels > 2) return TSMC_EINVAL;
   if (cfg->problem_base < 0 || (int64_t)cfg->problem_base + cfg->n_problems > INT32_MAX)
     return TSMC_EINVAL;
+  if (cfg->fused_rounds != 0 && cfg->fused_rounds != 1) return TSMC_EINVAL;
   if (cfg->channels == 2) {
     if (cfg->model != TSMC_SINUSOID) return TSMC_EINVAL;
     for (int q = 0; q < 4; ++q)
@@ -146,9 +149,10 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.logw = L.take(sizeof(double) * Ptot);
   o.cw = L.take(sizeof(double) * Ptot);
   o.anc = L.take(sizeof(int32_t) * Ptot);
-  o.acc = L.take(sizeof(double) * Ptot);
-  o.nleaf = L.take(sizeof(int32_t) * Ptot);
-  o.flags = L.take(sizeof(int32_t) * Ptot);
+  const int64_t rows = std::max<int64_t>(1, cfg->n_mut);   // per-round rows of the fused stage
+  o.acc = L.take(sizeof(double) * Ptot * rows);
+  o.nleaf = L.take(sizeof(int32_t) * Ptot * rows);
+  o.flags = L.take(sizeof(int32_t) * Ptot * rows);
   o.outcome = L.take(sizeof(int32_t) * Ptot);
   o.fis = L.take(sizeof(double) * Ptot * D);
   o.beta = L.take(sizeof(double) * cfg->n_problems);
@@ -164,6 +168,7 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.order_hist = L.take(sizeof(int32_t) * kOrderBuckets);
   o.kde = L.take(sizeof(double) * kKdeStride * cfg->n_problems);
   o.kcum = L.take(sizeof(int32_t) * Ptot);
+  o.next = L.take(sizeof(unsigned int) * 4);
   return o;
 }
 
@@ -251,8 +256,22 @@ tsmc_status prep_t(Ctx* c) {
   TRY(allow_smem(c, &k_eval<MODEL, PREC, R, true, false>));
   TRY(allow_smem(c, &k_eval<MODEL, PREC, R, false, false>));
   TRY(allow_smem(c, &k_rj<MODEL, PREC, R>));
-  if constexpr (PREC == FP64) TRY(allow_smem(c, &k_nuts<MODEL, PREC, R>));
-  else TRY(allow_smem(c, &k_nuts_mixed<MODEL, R>));
+  if constexpr (PREC == FP64) {
+    TRY(allow_smem(c, &k_nuts<MODEL, PREC, R>));
+  } else {
+    TRY(allow_smem(c, &k_nuts_mixed<MODEL, R>));
+    TRY(allow_smem(c, &k_mutate_mixed<MODEL, R>));
+    // resident blocks of the persistent mutation kernel (more would only start once the
+    // counter is spent; fewer would leave SM slots empty)
+    SmemPlan sp = smem_plan(c, false, c->cfg.max_depth);
+    const size_t sm = std::max(sp.nuts_mixed_kernel_bytes(), sp.rj_kernel_bytes());
+    int per_sm = 0, dev = 0, n_sm = 0;
+    TRY_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mutate_mixed<MODEL, R>,
+                                                              c->T, sm));
+    TRY_CUDA(c, cudaGetDevice(&dev));
+    TRY_CUDA(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    c->mut_grid = std::max(1, per_sm) * n_sm;
+  }
   return TSMC_OK;
 }
 
@@ -362,6 +381,28 @@ tsmc_status nuts_launch_t(Ctx* c, int round, NutsOut out) {
   }
 }
 
+template <int MODEL, int PREC, int R>
+tsmc_status mutate_launch_t(Ctx* c, int) {
+  if constexpr (PREC != MIXED) {
+    return fail(c, TSMC_EINVAL, "the fused mutation launch is a mixed-path kernel");
+  } else {
+    TRY(build_order(c, c->K));
+    KParams kp = kparams(c);
+    kp.order = c->order;
+    SmemPlan sp = smem_plan(c, false, c->cfg.max_depth);
+    const size_t sm = std::max(sp.nuts_mixed_kernel_bytes(), sp.rj_kernel_bytes());
+    auto fn = &k_mutate_mixed<MODEL, R>;
+    TRY(launch_prep(c, fn, sm));
+    TRY_CUDA(c, cudaMemsetAsync(c->next, 0, sizeof(unsigned int), c->stream));
+    const int grid = (int)std::min<int64_t>(c->mut_grid, c->Ptot);
+    pre(c, KC_NUTS);
+    fn<<<grid, c->T, sm, c->stream>>>(kp, c->cfg.n_mut, MutOut{c->outcome, c->acc, c->nleaf,
+                                                                c->flags},
+                                      sp, c->next, c->cfg.model != TSMC_PULSE_LINAMP ? 1 : 0);
+    return last_launch(c, "k_mutate_mixed");
+  }
+}
+
 #define DISPATCH(FN, ...)                                                                 \
   do {                                                                                    \
     const int m_ = c->cfg.model, p_ = c->cfg.precision;                                   \
@@ -389,6 +430,7 @@ tsmc_status eval_launch(Ctx* c, const EvalIO& io, bool grad, bool fisher) {
 }
 tsmc_status rj_launch(Ctx* c, int round, int32_t* outcome) { DISPATCH(rj_launch_t, round, outcome); }
 tsmc_status nuts_launch(Ctx* c, int round, NutsOut out) { DISPATCH(nuts_launch_t, round, out); }
+tsmc_status mutate_launch(Ctx* c) { DISPATCH(mutate_launch_t, 0); }
 
 tsmc_status require_ready(Ctx* c) {
   for (int p = 0; p < c->cfg.n_problems; ++p)
@@ -450,12 +492,21 @@ tsmc_status mutation_body(Ctx* c) {
   k_metric<<<np, 256, 0, c->stream>>>(c->fis, c->K, c->probs, P, c->D, c->minv);
   TRY(last_launch(c, "k_metric"));
   if (c->cfg.birth_proposal == 1 && c->cfg.model != TSMC_PULSE_LINAMP) TRY(kde_launch(c, -1));
-  for (int r = 0; r < c->cfg.n_mut; ++r) {
-    if (c->cfg.model != TSMC_PULSE_LINAMP) TRY(rj_launch(c, r, c->outcome));
-    TRY(nuts_launch(c, r, NutsOut{c->acc, c->nleaf, c->flags}));
+  if (c->cfg.precision == TSMC_MIXED && c->cfg.fused_rounds == 1 && c->cfg.n_mut > 0) {
+    // every round of every particle in one persistent launch (see k_mutate_mixed)
+    TRY(mutate_launch(c));
     pre(c, KC_OTHER);
-    k_round_stats<<<np, 256, 0, c->stream>>>(c->acc, c->nleaf, c->probs, P, c->stats);
-    TRY(last_launch(c, "k_round_stats"));
+    k_round_stats_all<<<np, 256, 0, c->stream>>>(c->acc, c->nleaf, c->probs, P, c->Ptot,
+                                                 c->cfg.n_mut, c->stats);
+    TRY(last_launch(c, "k_round_stats_all"));
+  } else {
+    for (int r = 0; r < c->cfg.n_mut; ++r) {
+      if (c->cfg.model != TSMC_PULSE_LINAMP) TRY(rj_launch(c, r, c->outcome));
+      TRY(nuts_launch(c, r, NutsOut{c->acc, c->nleaf, c->flags}));
+      pre(c, KC_OTHER);
+      k_round_stats<<<np, 256, 0, c->stream>>>(c->acc, c->nleaf, c->probs, P, c->stats);
+      TRY(last_launch(c, "k_round_stats"));
+    }
   }
   pre(c, KC_OTHER);
   k_eps_update<<<(np + 127) / 128, 128, 0, c->stream>>>(c->probs, c->stats, c->eps, np);
@@ -588,6 +639,7 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->order_hist = reinterpret_cast<int32_t*>(b + o.order_hist);
   c->kde = reinterpret_cast<double*>(b + o.kde);
   c->kcum = reinterpret_cast<int32_t*>(b + o.kcum);
+  c->next = reinterpret_cast<unsigned int*>(b + o.next);
   for (int p = 0; p < cfg->n_problems; ++p) c->nmax = std::max(c->nmax, (double)cap[p]);
   c->cap.assign(cap, cap + cfg->n_problems);
   c->off.resize(cfg->n_problems);

@@ -245,15 +245,16 @@ __device__ double kde_logq_block(const double* kde, const double* z, double eps,
   return mx + log(v[0]);
 }
 
+// one particle's move (all threads of the block call it; block-uniform exits)
 template <int MODEL, int PREC, int R>
-__global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcome, SmemPlan sp) {
+__device__ void rj_particle(const KParams& kp, int64_t gi, int round, int32_t* outcome,
+                            const SmemPlan& sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   __shared__ int s_move;       // 0 none, 1 birth, 2 death
   __shared__ int s_j;
   __shared__ double s_u;
   __shared__ double s_znew[4];
-  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const int pkey = prob + kp.prob_base;
   const uint64_t li = (uint64_t)(gi % kp.P);
@@ -432,6 +433,12 @@ __global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcom
     }
     if (outcome) outcome[gi] = out;
   }
+}
+
+template <int MODEL, int PREC, int R>
+__global__ void TSMC_PARTICLE_BOUNDS k_rj(KParams kp, int round, int32_t* outcome, SmemPlan sp) {
+  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
+  rj_particle<MODEL, PREC, R>(kp, gi, round, outcome, sp);
 }
 
 // ---------------------------------------------------------------------------
@@ -852,9 +859,10 @@ __device__ __forceinline__ float momentum_normal_f(uint64_t seed, int problem, u
   return (m & 1) ? rad * sn : rad * cs;
 }
 
+// one particle's transition (all threads of the block call it; block-uniform exits)
 template <int MODEL, int R>
-__global__ void __launch_bounds__(256, 2) k_nuts_mixed(KParams kp, int round, NutsOut out,
-                                                         SmemPlan sp) {
+__device__ void nuts_particle_mixed(const KParams& kp, int64_t gi, int round, NutsOut out,
+                                    const SmemPlan& sp) {
   extern __shared__ __align__(16) char smem[];
   constexpr int D = model_d<MODEL>();
   __shared__ int s_flag[8];
@@ -865,7 +873,6 @@ __global__ void __launch_bounds__(256, 2) k_nuts_mixed(KParams kp, int round, Nu
   __shared__ float s_minv[4];
   __shared__ int s_dir[kMaxDepth];
   __shared__ float s_utop[kMaxDepth];
-  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const int pkey = prob + kp.prob_base;
   const uint64_t li = (uint64_t)(gi % kp.P);
@@ -1104,6 +1111,59 @@ __global__ void __launch_bounds__(256, 2) k_nuts_mixed(KParams kp, int round, Nu
                                        (unsigned long long)(leaves + 1));
         atomicAdd(kp.cs_count + 3, cs_done);
       }
+    }
+  }
+}
+
+template <int MODEL, int R>
+__global__ void __launch_bounds__(256, 2) k_nuts_mixed(KParams kp, int round, NutsOut out,
+                                                         SmemPlan sp) {
+  const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
+  nuts_particle_mixed<MODEL, R>(kp, gi, round, out, sp);
+}
+
+// ---------------------------------------------------------------------------
+// The mutation rounds of a stage in one persistent launch (mixed path): within a stage the
+// step size, the metric and the birth proposal are fixed, so a particle's rounds (birth /
+// death, then a NUTS transition, n_mut times) depend on no other particle.  Each block
+// takes the next particle from a counter, in the longest-first order, and runs all its
+// rounds; a block whose particle finishes early takes another one instead of idling at
+// the end of a per-round launch behind the deepest trees.  Blocks never wait on one another
+// (the counter is their only shared state), so any grid size is safe; the host launches as
+// many blocks as are resident at once.  Per-round outputs go to [round][particle] rows.
+// Opt-in (tsmc_config.fused_rounds): with longest-first ordering the per-round launches
+// keep their slots busy to within a few percent, and this larger kernel computes ~8% fewer
+// component*samples per second than the separate ones on the pulse and band workloads.
+// ---------------------------------------------------------------------------
+struct MutOut {
+  int32_t* outcome;   // [Ptot] birth/death outcome of the last round
+  double* acc;        // [n_rounds][Ptot]
+  int32_t* nleaf;     // [n_rounds][Ptot]
+  int32_t* flags;     // [n_rounds][Ptot]
+};
+
+template <int MODEL, int R>
+__global__ void __launch_bounds__(256, 2) k_mutate_mixed(KParams kp, int n_rounds, MutOut mo,
+                                                           SmemPlan sp, unsigned int* next,
+                                                           int rj) {
+  __shared__ unsigned int s_item;
+  const unsigned int total = (unsigned int)(kp.n_problems * kp.P);
+  const int64_t Ptot = (int64_t)total;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
+    __syncthreads();
+    const unsigned int item = s_item;
+    __syncthreads();   // every thread has read s_item before it is written again
+    if (item >= total) return;
+    const int64_t gi = kp.order ? (int64_t)kp.order[item] : (int64_t)item;
+    for (int r = 0; r < n_rounds; ++r) {
+      if (rj) {
+        rj_particle<MODEL, MIXED, R>(kp, gi, r, mo.outcome, sp);
+        __syncthreads();
+      }
+      NutsOut no{mo.acc + r * Ptot, mo.nleaf + r * Ptot, mo.flags + r * Ptot};
+      nuts_particle_mixed<MODEL, R>(kp, gi, r, no, sp);
+      __syncthreads();
     }
   }
 }
@@ -1409,6 +1469,24 @@ __global__ void k_metric(const double* fis_sum, const int32_t* K, const ProbDev*
       if (!(h > 1e-8)) h = 1e-8;
       minv[4 * prob + d] = 1.0 / h;
     }
+  }
+}
+
+// acceptance statistics of n_rounds rounds stored as [round][Ptot] rows, added round by
+// round in the order of k_round_stats (one launch instead of one per round)
+__global__ void k_round_stats_all(const double* acc, const int32_t* nleaf, const ProbDev* probs,
+                                  int P, int64_t Ptot, int n_rounds, double* stats) {
+  __shared__ double red[64];
+  const int prob = blockIdx.x;
+  if (probs[prob].done) return;
+  for (int r = 0; r < n_rounds; ++r) {
+    double v[2] = {0, 0};
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      const int64_t g = r * Ptot + (int64_t)prob * P + i;
+      if (nleaf[g] > 0) { v[0] += acc[g]; v[1] += 1.0; }
+    }
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) { stats[2 * prob] += v[0]; stats[2 * prob + 1] += v[1]; }
   }
 }
 

@@ -10,9 +10,12 @@ posterior-start): data arrive in segments, each 20 s longer than the last.
 Reported per segment: SMC stages to reach beta = 1, log Z (increments summed along the
 posterior-start chain), the posterior over K and the wall time.
 
-Also: the population birth proposal against prior births, and the throughput of the batched
+Also: the population birth proposal against prior births; the throughput of the batched
 logL + gradient evaluation per precision (``python -m paper_2609_17674_b300.experiments eval
---precision fp64``, one JSON line).
+--precision fp64``); NUTS transitions of one workload after a few stages (``... nuts
+--workload gb --particles 512``, the small case of the kernel profiles); and the posterior
+start over 2^17, 2^18 and 2^19 samples at P = 16384 (``... assimilation``).  Each prints one
+JSON line.
 """
 from __future__ import annotations
 
@@ -181,6 +184,91 @@ def eval_throughput(wl: Workload, precision: int, reps: int = 3, seed: int = 1,
                 ms_per_launch=best, cs_per_s=cs / (best * 1e-3))
 
 
+def nuts_launch_timing(wl: Workload, precision: int = capi.MIXED, warm_stages: int = 3,
+                       launches: int = 3) -> dict:
+    """A prior start of the workload, warm_stages SMC stages, then `launches` NUTS transitions
+    of the population, each timed with CUDA events on the context's stream; returns the
+    fastest with the component*samples it evaluated (nominal and computed)."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    ctx = sampler.open_context(wl, precision, stream=stream)
+    ctx.init_population()
+    for st in range(warm_stages):
+        ctx.run_stage(st, use_graph=False, read=False)
+    torch.cuda.synchronize()
+    best = None
+    for r in range(launches):
+        ctx.counters(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.nuts_move(warm_stages, r)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        (_, cs, _, cc), _ = ctx.counters(reset=True)
+        ms = e0.elapsed_time(e1)
+        if best is None or ms < best[0]:
+            best = (ms, cs, cc)
+    ctx.close()
+    ms, cs, cc = best
+    return dict(workload=wl.name, precision="fp64" if precision == capi.FP64 else "mixed",
+                ms=ms, cs_nominal=cs, cs_computed=cc, nominal_cs_per_s=cs / (ms * 1e-3),
+                computed_cs_per_s=cc / (ms * 1e-3))
+
+
+def assimilation_experiment(P: int = 16384, sizes=(1 << 17, 1 << 18, 1 << 19),
+                            precision: int = capi.MIXED, max_stages: int = 400,
+                            prior_start: bool = True) -> dict:
+    """Posterior start on the assimilation workload (K_true = 14 pulses on t_n = n / 2^19):
+    a prior start on the first sizes[0] samples, then for every later size the new samples are
+    assimilated (Eq. reuse_bridge) and the run continues from the previous posterior; with
+    prior_start, also a prior start on each size.  Per segment: SMC stages, wall time,
+    component*sample evaluations per second (device counters), log Z and mean K."""
+    import torch
+
+    from . import synth
+
+    wl = synth.assimilation_pulse_k14(P=P, n_full=sizes[-1])
+    pr = wl.problems[0]
+
+    def run(ctx, **kw):
+        ctx.counters(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = sampler.run_smc(ctx, max_stages=max_stages, **kw)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        (ce, cn, _, _), _ = ctx.counters(reset=True)
+        return out, wall, (ce + cn) / wall
+
+    def summary(ctx, n, out, wall, rate, logz):
+        K = ctx.get_population()[1].cpu().numpy()
+        return dict(samples=n, stages=out["n_stages"], wall_s=round(wall, 3), cs_per_s=rate,
+                    logz=logz, reached=bool(out["beta"][-1][0] >= 1.0), mean_k=float(K.mean()))
+
+    res = dict(workload=wl.name, P=P, sizes=list(sizes), posterior=[], prior=[])
+    ctx = sampler.open_context(wl, precision, n_use=sizes[0], n_capacity=[pr.n])
+    logz = 0.0
+    for i, n in enumerate(sizes):
+        if i == 0:
+            out, wall, rate = run(ctx)
+        else:
+            if not res["posterior"][-1]["reached"]:
+                raise RuntimeError("segment stopped at beta < 1: no posterior to start from")
+            ctx.assimilate(0, pr.d[sizes[i - 1]:n])
+            out, wall, rate = run(ctx, stage0=1000 * i, init_prior=False)
+        logz += float(out["logz"][-1][0])
+        res["posterior"].append(summary(ctx, n, out, wall, rate, logz))
+    ctx.close()
+    if prior_start:
+        for n in sizes[1:]:
+            ctx = sampler.open_context(wl, precision, n_use=n, n_capacity=[pr.n])
+            out, wall, rate = run(ctx)
+            res["prior"].append(summary(ctx, n, out, wall, rate, float(out["logz"][-1][0])))
+            ctx.close()
+    return res
+
+
 def _main(argv=None):
     import argparse
     import json
@@ -194,10 +282,30 @@ def _main(argv=None):
     ev.add_argument("--particles", type=int, default=8192)
     ev.add_argument("--samples", type=int, default=16384)
     ev.add_argument("--reps", type=int, default=3)
+    nu = sub.add_parser("nuts", help="NUTS transitions after a few SMC stages (one workload)")
+    nu.add_argument("--workload", choices=["pulse", "gb", "gb_ae"], default="pulse")
+    nu.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    nu.add_argument("--particles", type=int, default=1024)
+    nu.add_argument("--warm-stages", type=int, default=3)
+    nu.add_argument("--launches", type=int, default=3)
+    asm = sub.add_parser("assimilation", help="posterior start over 2^17, 2^18, 2^19 samples")
+    asm.add_argument("--particles", type=int, default=16384)
+    asm.add_argument("--max-stages", type=int, default=400)
+    asm.add_argument("--no-prior-start", action="store_true")
     a = ap.parse_args(argv)
-    wl = synth.pulse_k20(P=a.particles, n=a.samples)
-    prec = capi.FP64 if a.precision == "fp64" else capi.MIXED
-    print(json.dumps(eval_throughput(wl, prec, reps=a.reps)))
+    prec = capi.FP64 if getattr(a, "precision", "mixed") == "fp64" else capi.MIXED
+    if a.cmd == "eval":
+        wl = synth.pulse_k20(P=a.particles, n=a.samples)
+        print(json.dumps(eval_throughput(wl, prec, reps=a.reps)))
+    elif a.cmd == "nuts":
+        wl = {"pulse": lambda: synth.pulse_k20(P=a.particles),
+              "gb": lambda: synth.gb_band_k10(P=a.particles),
+              "gb_ae": lambda: synth.ae_workload(f"gb_ae_n262144x2_k10_p{a.particles}", 1 << 18,
+                                                 10, 30, a.particles, 1007)}[a.workload]()
+        print(json.dumps(nuts_launch_timing(wl, prec, a.warm_stages, a.launches)))
+    else:
+        print(json.dumps(assimilation_experiment(a.particles, max_stages=a.max_stages,
+                                                 prior_start=not a.no_prior_start)))
 
 
 if __name__ == "__main__":

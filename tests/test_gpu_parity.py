@@ -526,6 +526,33 @@ def test_stage_graph_matches_eager():
             np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("model,schedule", [("pulse", 0), ("pulse", 1), ("sinusoid", 0)])
+def test_fused_mutation_rounds_match_per_round_launches(model, schedule):
+    """The mixed path's persistent launch of a stage's rounds (each block pulls particles and
+    runs all their rounds) gives bit for bit the results of one launch per move and round:
+    the same particles, K, likelihoods and step size after three stages, eager and graph."""
+    res = []
+    for fused, graph in ((0, False), (1, False), (1, True)):
+        wl = (synth.pulse_workload("t", 3000, 3, 8, 200, 61) if model == "pulse"
+              else synth.sinusoid_workload("t", 4000, 3, 6, 150, 62))
+        if schedule == 1:
+            wl.schedule, wl.p_nuts, wl.p_birth, wl.p_death = capi.SCHED_MIXTURE, 0.6, 0.2, 0.2
+        wl.n_mut = 3
+        ctx = sampler.open_context(wl, capi.MIXED, fused_rounds=fused)
+        ctx.init_population()
+        out = [ctx.run_stage(s, use_graph=graph) for s in range(3)]
+        z, K, lo, ln = (x.cpu().numpy() for x in ctx.get_population())
+        eps, minv = ctx.get_kernel_params()
+        res.append((out, z, K, lo, ln, eps, minv))
+        ctx.close()
+    for other in res[1:]:
+        for a, b in zip(res[0][1:], other[1:]):
+            np.testing.assert_array_equal(a, b)
+        for sa, sb in zip(res[0][0], other[0]):
+            for x, y in zip(sa, sb):
+                np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("seed", [1001, 7, 8])
 def test_smc_stage_matches_oracle_fp64(seed):
     """One full stage (temper, resample, metric, RJ + NUTS rounds) on both sides: the same
