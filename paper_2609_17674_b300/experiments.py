@@ -218,7 +218,7 @@ def nuts_launch_timing(wl: Workload, precision: int = capi.MIXED, warm_stages: i
 
 def assimilation_experiment(P: int = 16384, sizes=(1 << 17, 1 << 18, 1 << 19),
                             precision: int = capi.MIXED, max_stages: int = 400,
-                            prior_start: bool = True) -> dict:
+                            prior_start: bool = True, posterior_start: bool = True) -> dict:
     """Posterior start on the assimilation workload (K_true = 14 pulses on t_n = n / 2^19):
     a prior start on the first sizes[0] samples, then for every later size the new samples are
     assimilated (Eq. reuse_bridge) and the run continues from the previous posterior; with
@@ -249,7 +249,7 @@ def assimilation_experiment(P: int = 16384, sizes=(1 << 17, 1 << 18, 1 << 19),
     res = dict(workload=wl.name, P=P, sizes=list(sizes), posterior=[], prior=[])
     ctx = sampler.open_context(wl, precision, n_use=sizes[0], n_capacity=[pr.n])
     logz = 0.0
-    for i, n in enumerate(sizes):
+    for i, n in enumerate(sizes if posterior_start else []):
         if i == 0:
             out, wall, rate = run(ctx)
         else:
@@ -292,6 +292,7 @@ def _main(argv=None):
     asm.add_argument("--particles", type=int, default=16384)
     asm.add_argument("--max-stages", type=int, default=400)
     asm.add_argument("--no-prior-start", action="store_true")
+    asm.add_argument("--no-posterior-start", action="store_true")
     a = ap.parse_args(argv)
     prec = capi.FP64 if getattr(a, "precision", "mixed") == "fp64" else capi.MIXED
     if a.cmd == "eval":
@@ -305,7 +306,8 @@ def _main(argv=None):
         print(json.dumps(nuts_launch_timing(wl, prec, a.warm_stages, a.launches)))
     else:
         print(json.dumps(assimilation_experiment(a.particles, max_stages=a.max_stages,
-                                                 prior_start=not a.no_prior_start)))
+                                                 prior_start=not a.no_prior_start,
+                                                 posterior_start=not a.no_posterior_start)))
 
 
 if __name__ == "__main__":
