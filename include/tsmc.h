@@ -104,6 +104,13 @@ typedef struct {
                              the same results bit for bit; on the pulse and band workloads the
                              fused kernel computed 8% fewer component*samples per second.  The
                              FP64 path always launches per round. */
+  int32_t particles_global; /* 0: the context holds each problem's whole population.  Else
+                               the particles of each problem are sharded across processes
+                               (see the calls for a sharded population below): the whole population
+                               has particles_global particles per problem and this context
+                               holds particles [particle_base, particle_base + particles) */
+  int32_t particle_base;  /* global index of the context's first particle (Philox counter
+                             word 0 = particle_base + local index), 0 unless sharded */
 } tsmc_config;
 
 /* Opaque context: created by tsmc_create, released by tsmc_destroy. */
@@ -262,6 +269,45 @@ tsmc_status tsmc_counters(tsmc_ctx* ctx, uint64_t* cs_evals_host, int64_t* launc
  * creates that many events up front (two per recorded launch). */
 tsmc_status tsmc_profile(tsmc_ctx* ctx, int32_t enable);
 tsmc_status tsmc_profile_read(tsmc_ctx* ctx, int64_t* launches_host, double* ms_host, int32_t reset);
+
+/* A population sharded across processes (Sec. 6: moves are independent per particle, the
+ * reweighting, ESS and resampling are the global steps).  Each process holds a block of every
+ * problem's particles in a context with particles_global and particle_base set, draws the
+ * random numbers of those global particle indices, and joins the others with its own
+ * collectives; a stage is:
+ *   1. all-gather every shard's ll_new (tsmc_get_population) into ell [n_problems][P_global]
+ *      in global particle order;
+ *   2. tsmc_temper_resample_global: every process picks the same beta by ESS bisection,
+ *      adds the same evidence increment and draws the same systematic ancestors anc
+ *      [n_problems][P_global] (global indices) from the whole population;
+ *   3. exchange particles so that each process holds rows anc[i] for its own i, then
+ *      tsmc_load_population;
+ *   4. tsmc_metric_sums, all-reduce (sum) the [n_problems][5] sums, tsmc_metric_apply;
+ *   5. tsmc_mutation_rounds, all-reduce (sum) the [n_problems][2] acceptance statistics,
+ *      tsmc_eps_update_apply.
+ * With particles_global set, tsmc_run_stage and tsmc_temper_reweight_resample refuse with
+ * TSMC_ESTATE, and births from the population proposal are not available (EINVAL at create).
+ * All five calls are asynchronous on the context stream; device arrays as stated. */
+tsmc_status tsmc_temper_resample_global(tsmc_ctx* ctx, int32_t stage, const double* ell_dev,
+                                        int32_t* anc_dev);
+/* Replaces the context's particles (z [P_total][kmax][D], K, ll_old, ll_new on the device)
+ * and keeps beta, log Z, step size and metric; K outside [0, kmax] is clamped by the
+ * kernels. */
+tsmc_status tsmc_load_population(tsmc_ctx* ctx, const double* z_dev, const int32_t* K_dev,
+                                 const double* ll_old_dev, const double* ll_new_dev);
+/* Population sums of the metric over the context's particles, sums_dev [n_problems][5]:
+ * per parameter the sum of the particles' Gauss-Newton sums, then the sum of K (particles
+ * with a non-finite diagonal left out). */
+tsmc_status tsmc_metric_sums(tsmc_ctx* ctx, double* sums_dev);
+/* Metric from (all-reduced) sums: minv_d = 1 / max(1e-8, sum_d / sum K). */
+tsmc_status tsmc_metric_apply(tsmc_ctx* ctx, const double* sums_dev);
+/* The n_mut mutation rounds of a stage with the current step size and metric; writes the
+ * stage's acceptance statistics (sum over moved particles of the acceptance statistic,
+ * their number) per problem into stats_dev [n_problems][2]. */
+tsmc_status tsmc_mutation_rounds(tsmc_ctx* ctx, int32_t stage, double* stats_dev);
+/* Step-size update eps <- eps exp(sum / count - 0.8), clamped to [1e-4, 2], from
+ * (all-reduced) statistics [n_problems][2]. */
+tsmc_status tsmc_eps_update_apply(tsmc_ctx* ctx, const double* stats_dev);
 
 /* Systematic resampling without any device allocation and without a context.
  *

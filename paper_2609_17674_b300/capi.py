@@ -52,6 +52,12 @@ SIGNATURES = {
     "tsmc_profile": (I32, [P, I32]),
     "tsmc_profile_read": (I32, [P, P, P, I32]),
     "tsmc_resample_systematic_static": (I32, [P, I32, I32, U64, I32, P, P]),
+    "tsmc_temper_resample_global": (I32, [P, I32, P, P]),
+    "tsmc_load_population": (I32, [P, P, P, P, P]),
+    "tsmc_metric_sums": (I32, [P, P]),
+    "tsmc_metric_apply": (I32, [P, P]),
+    "tsmc_mutation_rounds": (I32, [P, I32, P]),
+    "tsmc_eps_update_apply": (I32, [P, P]),
     "tsmc_sync": (I32, [P]),
 }
 
@@ -70,6 +76,7 @@ class Config(C.Structure):
         ("birth_proposal", C.c_int32), ("birth_prior_weight", C.c_double),
         ("channels", C.c_int32), ("response", C.c_double * 4),
         ("problem_base", C.c_int32), ("fused_rounds", C.c_int32),
+        ("particles_global", C.c_int32), ("particle_base", C.c_int32),
     ]
 
 
@@ -310,6 +317,26 @@ class Context:
         ms = np.zeros(8)
         self._check(self.L.tsmc_profile_read(self.h, _ptr(n), _ptr(ms), 1 if reset else 0))
         return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    # ---- a population sharded across processes (see include/tsmc.h) ----
+    def temper_resample_global(self, stage, ell, anc):
+        self._check(self.L.tsmc_temper_resample_global(self.h, stage, _ptr(ell), _ptr(anc)))
+
+    def load_population(self, z, K, ll_old, ll_new):
+        self._check(self.L.tsmc_load_population(self.h, _ptr(z), _ptr(K), _ptr(ll_old),
+                                                _ptr(ll_new)))
+
+    def metric_sums(self, sums):
+        self._check(self.L.tsmc_metric_sums(self.h, _ptr(sums)))
+
+    def metric_apply(self, sums):
+        self._check(self.L.tsmc_metric_apply(self.h, _ptr(sums)))
+
+    def mutation_rounds(self, stage, stats):
+        self._check(self.L.tsmc_mutation_rounds(self.h, stage, _ptr(stats)))
+
+    def eps_update_apply(self, stats):
+        self._check(self.L.tsmc_eps_update_apply(self.h, _ptr(stats)))
 
     def sync(self):
         self._check(self.L.tsmc_sync(self.h))

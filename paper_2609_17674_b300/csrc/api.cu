@@ -46,6 +46,8 @@ struct tsmc_ctx {
   double* kde = nullptr;         // [n_problems][kKdeStride] population birth proposals
   int32_t* kcum = nullptr;       // [Ptot] prefix counts of K (scratch of the proposal build)
   unsigned int* next = nullptr;  // work counter of the persistent mutation launch
+  double* msums = nullptr;       // [n_problems][5] population sums of the metric
+  int64_t Pg = 0;                // particles per problem of the whole (sharded) population
   int mut_grid = 0;              // resident blocks of the persistent mutation kernel
   double nmax = 1.0;             // largest problem capacity (cost normalisation)
   cudaGraphExec_t graph = nullptr;
@@ -98,7 +100,7 @@ struct Layout {
 struct Offsets {
   size_t probs, d64, d32, z, z2, K, K2, llo, llo2, lln, lln2, logw, cw, anc, acc, nleaf, flags,
       outcome, fis, beta, logz, ess, eps, minv, stats, stage, tw, cs, order, order_hist, kde,
-      kcum, next;
+      kcum, next, msums;
 };
 
 tsmc_status check_cfg(const tsmc_config* cfg) {
@@ -119,6 +121,15 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
   if (cfg->problem_base < 0 || (int64_t)cfg->problem_base + cfg->n_problems > INT32_MAX)
     return TSMC_EINVAL;
   if (cfg->fused_rounds != 0 && cfg->fused_rounds != 1) return TSMC_EINVAL;
+  if (cfg->particles_global != 0) {
+    if (cfg->particles_global < cfg->particles || cfg->particle_base < 0 ||
+        (int64_t)cfg->particle_base + cfg->particles > cfg->particles_global)
+      return TSMC_EINVAL;
+    // the population birth proposal would be built from one shard only
+    if (cfg->birth_proposal == 1) return TSMC_EINVAL;
+  } else if (cfg->particle_base != 0) {
+    return TSMC_EINVAL;
+  }
   if (cfg->channels == 2) {
     if (cfg->model != TSMC_SINUSOID) return TSMC_EINVAL;
     for (int q = 0; q < 4; ++q)
@@ -146,9 +157,12 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.llo2 = L.take(sizeof(double) * Ptot);
   o.lln = L.take(sizeof(double) * Ptot);
   o.lln2 = L.take(sizeof(double) * Ptot);
-  o.logw = L.take(sizeof(double) * Ptot);
-  o.cw = L.take(sizeof(double) * Ptot);
-  o.anc = L.take(sizeof(int32_t) * Ptot);
+  // log-weights, prefix sums and ancestors cover the whole population when it is sharded
+  const int64_t Pw = (int64_t)cfg->n_problems *
+                     std::max<int64_t>(cfg->particles, cfg->particles_global);
+  o.logw = L.take(sizeof(double) * Pw);
+  o.cw = L.take(sizeof(double) * Pw);
+  o.anc = L.take(sizeof(int32_t) * Pw);
   const int64_t rows = std::max<int64_t>(1, cfg->n_mut);   // per-round rows of the fused stage
   o.acc = L.take(sizeof(double) * Ptot * rows);
   o.nleaf = L.take(sizeof(int32_t) * Ptot * rows);
@@ -169,6 +183,7 @@ Offsets plan(const tsmc_config* cfg, const int64_t* cap, Layout& L) {
   o.kde = L.take(sizeof(double) * kKdeStride * cfg->n_problems);
   o.kcum = L.take(sizeof(int32_t) * Ptot);
   o.next = L.take(sizeof(unsigned int) * 4);
+  o.msums = L.take(sizeof(double) * 5 * cfg->n_problems);
   return o;
 }
 
@@ -196,6 +211,7 @@ KParams kparams(Ctx* c) {
   kp.pa.window = (c->cfg.precision == TSMC_MIXED && c->cfg.pulse_window) ? 1 : 0;
   kp.seed = c->cfg.seed;
   kp.prob_base = c->cfg.problem_base;
+  kp.particle_base = c->cfg.particle_base;
   kp.tw = c->tw;
   kp.z = c->z;
   kp.K = c->K;
@@ -484,13 +500,38 @@ tsmc_status kde_launch(Ctx* c, int stage_arg) {
   return last_launch(c, "k_kde_build");
 }
 
-tsmc_status mutation_body(Ctx* c) {
+// population sums of the metric (a Gauss-Newton evaluation of the context population)
+tsmc_status metric_sums_launch(Ctx* c, double* sums) {
   EvalIO io{c->z, c->K, c->beta, c->llo, c->lln, nullptr, nullptr, c->fis};
   TRY(eval_launch(c, io, true, true));
-  const int np = c->cfg.n_problems, P = c->cfg.particles;
   pre(c, KC_METRIC);
-  k_metric<<<np, 256, 0, c->stream>>>(c->fis, c->K, c->probs, P, c->D, c->minv);
-  TRY(last_launch(c, "k_metric"));
+  k_metric_sums<<<c->cfg.n_problems, 256, 0, c->stream>>>(c->fis, c->K, c->probs,
+                                                           c->cfg.particles, c->D, sums);
+  return last_launch(c, "k_metric_sums");
+}
+
+tsmc_status metric_apply_launch(Ctx* c, const double* sums) {
+  const int np = c->cfg.n_problems;
+  pre(c, KC_METRIC);
+  k_metric_apply<<<(np + 127) / 128, 128, 0, c->stream>>>(sums, c->probs, np, c->D, c->minv);
+  return last_launch(c, "k_metric_apply");
+}
+
+// the n_mut mutation rounds of a stage (statistics accumulate in c->stats)
+tsmc_status rounds_body(Ctx* c);
+
+tsmc_status mutation_body(Ctx* c) {
+  const int np = c->cfg.n_problems;
+  TRY(metric_sums_launch(c, c->msums));
+  TRY(metric_apply_launch(c, c->msums));
+  TRY(rounds_body(c));
+  pre(c, KC_OTHER);
+  k_eps_update<<<(np + 127) / 128, 128, 0, c->stream>>>(c->probs, c->stats, c->eps, np);
+  return last_launch(c, "k_eps_update");
+}
+
+tsmc_status rounds_body(Ctx* c) {
+  const int np = c->cfg.n_problems, P = c->cfg.particles;
   if (c->cfg.birth_proposal == 1 && c->cfg.model != TSMC_PULSE_LINAMP) TRY(kde_launch(c, -1));
   if (c->cfg.precision == TSMC_MIXED && c->cfg.fused_rounds == 1 && c->cfg.n_mut > 0) {
     // every round of every particle in one persistent launch (see k_mutate_mixed)
@@ -508,9 +549,7 @@ tsmc_status mutation_body(Ctx* c) {
       TRY(last_launch(c, "k_round_stats"));
     }
   }
-  pre(c, KC_OTHER);
-  k_eps_update<<<(np + 127) / 128, 128, 0, c->stream>>>(c->probs, c->stats, c->eps, np);
-  return last_launch(c, "k_eps_update");
+  return TSMC_OK;
 }
 
 tsmc_status temper_resample(Ctx* c, int stage) {
@@ -640,6 +679,8 @@ tsmc_status tsmc_create(const tsmc_config* cfg, const int64_t* cap, void* ws, si
   c->kde = reinterpret_cast<double*>(b + o.kde);
   c->kcum = reinterpret_cast<int32_t*>(b + o.kcum);
   c->next = reinterpret_cast<unsigned int*>(b + o.next);
+  c->msums = reinterpret_cast<double*>(b + o.msums);
+  c->Pg = std::max<int64_t>(cfg->particles, cfg->particles_global);
   for (int p = 0; p < cfg->n_problems; ++p) c->nmax = std::max(c->nmax, (double)cap[p]);
   c->cap.assign(cap, cap + cfg->n_problems);
   c->off.resize(cfg->n_problems);
@@ -912,17 +953,16 @@ tsmc_status tsmc_update_metric(tsmc_ctx* ctx) {
   Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
-  EvalIO io{c->z, c->K, c->beta, c->llo, c->lln, nullptr, nullptr, c->fis};
-  TRY(eval_launch(c, io, true, true));
-  pre(c, KC_METRIC);
-  k_metric<<<c->cfg.n_problems, 256, 0, c->stream>>>(c->fis, c->K, c->probs, c->cfg.particles, c->D, c->minv);
-  return last_launch(c, "k_metric");
+  TRY(metric_sums_launch(c, c->msums));
+  return metric_apply_launch(c, c->msums);
 }
 
 tsmc_status tsmc_temper_reweight_resample(tsmc_ctx* ctx, int32_t stage, double* beta_h,
                                           double* logz_h, double* ess_h) {
   Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
+  if (c->Pg != c->cfg.particles)
+    return fail(c, TSMC_ESTATE, "sharded population: use tsmc_temper_resample_global");
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (stage < 0) return fail(c, TSMC_EINVAL, "bad stage");
   TRY(temper_resample(c, stage));
@@ -947,6 +987,8 @@ tsmc_status tsmc_run_stage(tsmc_ctx* ctx, int32_t stage, int32_t use_graph, doub
                            double* logz_h, double* ess_h) {
   Ctx* c = ctx;
   if (!c) return TSMC_EINVAL;
+  if (c->Pg != c->cfg.particles)
+    return fail(c, TSMC_ESTATE, "sharded population: use tsmc_temper_resample_global");
   if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
   if (stage < 0) return fail(c, TSMC_EINVAL, "bad stage");
   TRY(set_stage(c, stage));
@@ -1072,6 +1114,92 @@ tsmc_status tsmc_profile_read(tsmc_ctx* ctx, int64_t* launches_host, double* ms_
     c->recs.clear();
   }
   return TSMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A population sharded across processes (tsmc_config.particles_global): the calls that
+// take or give the population-wide quantities, so that the caller's collectives join the
+// shards (see include/tsmc.h).
+// ---------------------------------------------------------------------------
+tsmc_status tsmc_temper_resample_global(tsmc_ctx* ctx, int32_t stage, const double* ell_dev,
+                                        int32_t* anc_dev) {
+  Ctx* c = ctx;
+  if (!c) return TSMC_EINVAL;
+  if (!ell_dev || !anc_dev) return fail(c, TSMC_EINVAL, "null log-likelihoods or ancestors");
+  if (stage < 0) return fail(c, TSMC_EINVAL, "bad stage");
+  if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
+  const int np = c->cfg.n_problems;
+  const int P = (int)c->Pg;
+  TRY(set_stage(c, stage));
+  TemperIO tio{ell_dev, c->logw, c->beta, c->logz, c->ess, c->probs, c->cfg.alpha};
+  const int tt = P >= 1024 ? 1024 : ((P + 31) / 32) * 32;
+  pre(c, KC_TEMPER);
+  if (c->cfg.precision == TSMC_MIXED) {
+    k_temper_mixed<<<np, tt, 0, c->stream>>>(tio, P, reinterpret_cast<float*>(c->cw));
+    TRY(last_launch(c, "k_temper_mixed"));
+  } else {
+    k_temper<<<np, tt, 0, c->stream>>>(tio, P);
+    TRY(last_launch(c, "k_temper"));
+  }
+  pre(c, KC_RESAMPLE);
+  k_resample<<<np, tt, 0, c->stream>>>(c->logw, reinterpret_cast<long long*>(c->cw), anc_dev,
+                                       c->probs, c->cfg.seed, stage, P, c->cfg.problem_base);
+  return last_launch(c, "k_resample");
+}
+
+tsmc_status tsmc_load_population(tsmc_ctx* ctx, const double* z_dev, const int32_t* K_dev,
+                                 const double* llo_dev, const double* lln_dev) {
+  Ctx* c = ctx;
+  if (!c) return TSMC_EINVAL;
+  if (!z_dev || !K_dev || !llo_dev || !lln_dev) return fail(c, TSMC_EINVAL, "null argument");
+  TRY(require_ready(c));
+  TRY_CUDA(c, cudaMemcpyAsync(c->z, z_dev, sizeof(double) * c->Ptot * c->kd, cudaMemcpyDeviceToDevice, c->stream));
+  TRY_CUDA(c, cudaMemcpyAsync(c->K, K_dev, sizeof(int32_t) * c->Ptot, cudaMemcpyDeviceToDevice, c->stream));
+  TRY_CUDA(c, cudaMemcpyAsync(c->llo, llo_dev, sizeof(double) * c->Ptot, cudaMemcpyDeviceToDevice, c->stream));
+  TRY_CUDA(c, cudaMemcpyAsync(c->lln, lln_dev, sizeof(double) * c->Ptot, cudaMemcpyDeviceToDevice, c->stream));
+  c->pop_ready = true;
+  return TSMC_OK;
+}
+
+tsmc_status tsmc_metric_sums(tsmc_ctx* ctx, double* sums_dev) {
+  Ctx* c = ctx;
+  if (!c) return TSMC_EINVAL;
+  if (!sums_dev) return fail(c, TSMC_EINVAL, "null sums");
+  if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
+  return metric_sums_launch(c, sums_dev);
+}
+
+tsmc_status tsmc_metric_apply(tsmc_ctx* ctx, const double* sums_dev) {
+  Ctx* c = ctx;
+  if (!c) return TSMC_EINVAL;
+  if (!sums_dev) return fail(c, TSMC_EINVAL, "null sums");
+  return metric_apply_launch(c, sums_dev);
+}
+
+tsmc_status tsmc_mutation_rounds(tsmc_ctx* ctx, int32_t stage, double* stats_dev) {
+  Ctx* c = ctx;
+  if (!c) return TSMC_EINVAL;
+  if (!stats_dev) return fail(c, TSMC_EINVAL, "null statistics");
+  if (stage < 0) return fail(c, TSMC_EINVAL, "bad stage");
+  if (!c->pop_ready) return fail(c, TSMC_ESTATE, "no population");
+  const size_t nb = sizeof(double) * 2 * c->cfg.n_problems;
+  TRY_CUDA(c, cudaMemsetAsync(c->stats, 0, nb, c->stream));
+  TRY(set_stage(c, stage));
+  TRY(rounds_body(c));
+  TRY_CUDA(c, cudaMemcpyAsync(stats_dev, c->stats, nb, cudaMemcpyDeviceToDevice, c->stream));
+  return cuda_check(c, cudaMemsetAsync(c->stats, 0, nb, c->stream), "clear statistics");
+}
+
+tsmc_status tsmc_eps_update_apply(tsmc_ctx* ctx, const double* stats_dev) {
+  Ctx* c = ctx;
+  if (!c) return TSMC_EINVAL;
+  if (!stats_dev) return fail(c, TSMC_EINVAL, "null statistics");
+  const int np = c->cfg.n_problems;
+  TRY_CUDA(c, cudaMemcpyAsync(c->stats, stats_dev, sizeof(double) * 2 * np,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  pre(c, KC_OTHER);
+  k_eps_update<<<(np + 127) / 128, 128, 0, c->stream>>>(c->probs, c->stats, c->eps, np);
+  return last_launch(c, "k_eps_update");
 }
 
 // ---------------------------------------------------------------------------

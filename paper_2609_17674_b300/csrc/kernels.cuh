@@ -19,6 +19,7 @@ struct KParams {
   PriorArgs pa;
   uint64_t seed;
   int32_t prob_base;         // Philox key word 1 = prob_base + problem index
+  int64_t particle_base;     // Philox counter word 0 = particle_base + local particle index
   const double* tw;          // LINAMP fixed (t0, w), [kmax][2]
   double* z;                 // [Ptot][kmax][D]
   int32_t* K;                // [Ptot]
@@ -162,7 +163,7 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
   if (gi >= Ptot) return;
   const int prob = (int)(gi / kp.P);
   const int pkey = prob + kp.prob_base;
-  const uint64_t li = (uint64_t)(gi % kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P) + (uint64_t)kp.particle_base;
   const int kd = kp.kmax * kp.D;
   double* z = kp.z + gi * kd;
   for (int j = 0; j < kd; ++j) z[j] = 0.0;
@@ -257,7 +258,7 @@ __device__ void rj_particle(const KParams& kp, int64_t gi, int round, int32_t* o
   __shared__ double s_znew[4];
   const int prob = (int)(gi / kp.P);
   const int pkey = prob + kp.prob_base;
-  const uint64_t li = (uint64_t)(gi % kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P) + (uint64_t)kp.particle_base;
   __shared__ ProbDev s_pb;
   const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
   if (pb.done) return;
@@ -567,7 +568,7 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   const int64_t gi = kp.order ? (int64_t)kp.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int prob = (int)(gi / kp.P);
   const int pkey = prob + kp.prob_base;
-  const uint64_t li = (uint64_t)(gi % kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P) + (uint64_t)kp.particle_base;
   __shared__ ProbDev s_pb;
   const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
   if (pb.done) return;
@@ -875,7 +876,7 @@ __device__ void nuts_particle_mixed(const KParams& kp, int64_t gi, int round, Nu
   __shared__ float s_utop[kMaxDepth];
   const int prob = (int)(gi / kp.P);
   const int pkey = prob + kp.prob_base;
-  const uint64_t li = (uint64_t)(gi % kp.P);
+  const uint64_t li = (uint64_t)(gi % kp.P) + (uint64_t)kp.particle_base;
   __shared__ ProbDev s_pb;
   const ProbDev& pb = stage_problem(kp.probs, prob, s_pb);
   if (pb.done) return;
@@ -1448,8 +1449,11 @@ __global__ void k_gather(const int32_t* anc, const ProbDev* probs, int P, int kd
 // ---------------------------------------------------------------------------
 // Metric (the mass matrix of Sec. 3.2) and step size (one block per problem)
 // ---------------------------------------------------------------------------
-__global__ void k_metric(const double* fis_sum, const int32_t* K, const ProbDev* probs, int P,
-                         int D, double* minv) {
+// population sums of the metric per problem: sums[prob][0..3] = sum over particles of the
+// per-particle Gauss-Newton sums, sums[prob][4] = sum of K (particles with a non-finite
+// diagonal left out)
+__global__ void k_metric_sums(const double* fis_sum, const int32_t* K, const ProbDev* probs, int P,
+                              int D, double* sums) {
   __shared__ double red[160];
   const int prob = blockIdx.x;
   if (probs[prob].done) return;
@@ -1463,12 +1467,20 @@ __global__ void k_metric(const double* fis_sum, const int32_t* K, const ProbDev*
     v[4] += (double)K[g];
   }
   block_sum<5>(v, red);
-  if (threadIdx.x == 0) {
-    for (int d = 0; d < 4; ++d) {
-      double h = (d < D && v[4] > 0.0) ? v[d] / v[4] : 1.0;
-      if (!(h > 1e-8)) h = 1e-8;
-      minv[4 * prob + d] = 1.0 / h;
-    }
+  if (threadIdx.x < 5) sums[5 * prob + threadIdx.x] = v[threadIdx.x];
+}
+
+// M^-1 from the population sums: minv_d = 1 / max(1e-8, sum_d / sum K)  (unit metric when
+// no component exists)
+__global__ void k_metric_apply(const double* sums, const ProbDev* probs, int n_problems, int D,
+                               double* minv) {
+  const int prob = blockIdx.x * blockDim.x + threadIdx.x;
+  if (prob >= n_problems || probs[prob].done) return;
+  const double* v = sums + 5 * prob;
+  for (int d = 0; d < 4; ++d) {
+    double h = (d < D && v[4] > 0.0) ? v[d] / v[4] : 1.0;
+    if (!(h > 1e-8)) h = 1e-8;
+    minv[4 * prob + d] = 1.0 / h;
   }
 }
 

@@ -15,7 +15,9 @@ from .synth import Workload
 
 def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
                 samples_per_thread: int = 0, pulse_window: int = 1,
-                fused_rounds: int = 0) -> capi.Config:
+                fused_rounds: int = 0, particle_shard=None) -> capi.Config:
+    """particle_shard = (particle_base, particles_global): the context holds wl.P particles
+    of each problem starting at particle_base, of particles_global in all."""
     return capi.Config(model=wl.model, precision=precision, schedule=wl.schedule,
                        n_problems=len(wl.problems), particles=wl.P, kmax=wl.kmax, kmin=wl.kmin,
                        birth_proposal=wl.birth_proposal,
@@ -26,14 +28,17 @@ def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
                        amp_sd=wl.amp_sd, seed=wl.seed, threads=threads,
                        samples_per_thread=samples_per_thread,
                        pulse_window=pulse_window if precision == capi.MIXED else 0,
-                       problem_base=wl.problem_base, fused_rounds=fused_rounds)
+                       problem_base=wl.problem_base, fused_rounds=fused_rounds,
+                       particle_base=particle_shard[0] if particle_shard else 0,
+                       particles_global=particle_shard[1] if particle_shard else 0)
 
 
 def open_context(wl: Workload, precision=capi.MIXED, n_use=None, n_capacity=None, threads=0,
                  samples_per_thread=0, stream=None, pulse_window=1,
-                 fused_rounds=0) -> capi.Context:
+                 fused_rounds=0, particle_shard=None) -> capi.Context:
     """Context with every problem's data uploaded (first n_use samples of each)."""
-    cfg = make_config(wl, precision, threads, samples_per_thread, pulse_window, fused_rounds)
+    cfg = make_config(wl, precision, threads, samples_per_thread, pulse_window, fused_rounds,
+                      particle_shard)
     nb = len(wl.problems)
     n_use = n_use or [p.n for p in wl.problems]
     if np.isscalar(n_use):

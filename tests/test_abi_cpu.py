@@ -68,6 +68,28 @@ def test_workspace_bytes_and_config_validation():
     assert L.tsmc_workspace_bytes(C.byref(cfg), neg.ctypes.data, C.byref(nb)) == capi.EINVAL
 
 
+def test_particle_shard_configuration_rules():
+    """particles_global: at least the local count, the local block inside it, no population
+    birth proposal (it would be built from one shard); particle_base only when sharded."""
+    L = capi.lib()
+    wl = synth.pulse_n1024_k3()
+    cap = np.array([1024], dtype=np.int64)
+    nb = C.c_size_t(0)
+
+    def status(**kw):
+        cfg = make_config(wl, capi.FP64)
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        return L.tsmc_workspace_bytes(C.byref(cfg), cap.ctypes.data, C.byref(nb))
+
+    assert status(particles_global=2048, particle_base=1024) == capi.OK
+    assert status(particles_global=256) == capi.EINVAL          # fewer than the local 512
+    assert status(particles_global=1000, particle_base=600) == capi.EINVAL
+    assert status(particle_base=5) == capi.EINVAL
+    assert status(particles_global=2048, birth_proposal=1) == capi.EINVAL
+    assert status(fused_rounds=2) == capi.EINVAL
+
+
 def test_create_rejects_misaligned_workspace_without_device_work():
     L = capi.lib()
     wl = synth.pulse_n1024_k3()

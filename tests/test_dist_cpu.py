@@ -91,3 +91,82 @@ def test_bands_sharded_across_two_ranks_gloo():
     assert sorted(sum(owned, [])) == list(range(7)) and owned == out[1][1]
     assert all(o[2] == 4.0 for o in out)            # slowest rank
     assert all(o[3] == o[4] for o in out)           # every band counted once
+
+
+def test_exchange_plan_delivers_every_ancestor_row():
+    """Brute force: after the planned exchange every rank holds, in its own order, exactly the
+    rows the ancestors name (ragged shards, two problems, ancestors from anywhere)."""
+    import numpy as np
+
+    rng = np.random.default_rng(5)
+    for P_glob, world in ((10, 3), (64, 2), (7, 4), (1, 1)):
+        n_prob = 2
+        shards = tdist.particle_shards(P_glob, world)
+        assert sum(c for _, c in shards) == P_glob
+        anc = np.sort(rng.integers(0, P_glob, (n_prob, P_glob)), axis=1)
+        local = []   # row ids (problem, global particle) held by each rank, in its order
+        for b, c in shards:
+            local.append([(q, b + j) for q in range(n_prob) for j in range(c)])
+        plans = [tdist.exchange_plan(anc, shards, r) for r in range(world)]
+        for r in range(world):
+            recv = []
+            for s_ in range(world):
+                recv += [local[s_][i] for i in plans[s_][0][r]]
+            assert len(recv) == int(plans[r][1].sum())
+            got = [recv[t] for t in plans[r][2]]
+            b, c = shards[r]
+            want = [(q, int(anc[q, b + j])) for q in range(n_prob) for j in range(c)]
+            assert got == want
+
+
+def _exchange_worker(rank, world, port, q):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    P_glob, n_prob = 37, 2
+    shards = tdist.particle_shards(P_glob, world)
+    b, c = shards[rank]
+    ids = torch.tensor([[1000.0 * qq + b + j for j in range(c)] for qq in range(n_prob)])
+    full = tdist.all_gather_particles(ids, shards)          # every rank: all ids, global order
+    anc = np.sort(np.random.default_rng(3).integers(0, P_glob, (n_prob, P_glob)), axis=1)
+    rows = torch.stack([ids.ravel(), -ids.ravel()], dim=1)    # two columns per row
+    new = tdist.exchange_rows(rows, anc, shards, rank)
+    s = torch.tensor([float(rank + 1)])
+    tdist.all_reduce_sum(s)
+    q.put((rank, full.numpy().tolist(), new.numpy().tolist(), float(s[0])))
+    dist.destroy_process_group()
+
+
+def test_particle_exchange_two_ranks_gloo():
+    """2 gloo ranks, 37 particles of 2 problems: the all-gather returns every rank's block in
+    global order and the exchange leaves each rank with the rows of its ancestors."""
+    import numpy as np
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    procs = [ctx.Process(target=_exchange_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    P_glob = 37
+    anc = np.sort(np.random.default_rng(3).integers(0, P_glob, (2, P_glob)), axis=1)
+    shards = tdist.particle_shards(P_glob, 2)
+    for rank, full, new, s in out:
+        assert np.array_equal(np.array(full), [[1000.0 * qq + i for i in range(P_glob)]
+                                               for qq in range(2)])
+        b, c = shards[rank]
+        want = [1000.0 * qq + anc[qq, b + j] for qq in range(2) for j in range(c)]
+        assert [row[0] for row in new] == want and [row[1] for row in new] == [-w for w in want]
+        assert s == 3.0

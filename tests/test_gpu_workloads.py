@@ -194,3 +194,79 @@ def test_sharded_bands_reproduce_the_whole_set_fp64():
     parts = [run(tdist.shard_problems(full, 2, r)[0]) for r in range(2)]
     for i in range(5):
         assert np.array_equal(np.concatenate([p[i] for p in parts]), whole[i]), i
+
+
+def _particle_shard_worker(rank, world, port, q, P_glob, stages):
+    import copy
+    import os
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_17674_b300 import capi, sampler, synth
+    from paper_2609_17674_b300 import dist as tdist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)   # host-side collectives
+    torch.cuda.set_device(0)
+    wl = synth.pulse_workload("shard", 2048, 3, 6, P_glob, 77, n_mut=2)
+    shards = tdist.particle_shards(P_glob, world)
+    b, c = shards[rank]
+    wl_r = copy.copy(wl)
+    wl_r.P = c
+    ctx = sampler.open_context(wl_r, capi.FP64, particle_shard=(b, P_glob))
+    ctx.init_population()
+    hist = []
+    for st in range(stages):
+        beta, logz, _ = tdist.sharded_stage(ctx, st, shards, rank)
+        hist.append((float(beta[0]), float(logz[0])))
+    z, K, _, _ = ctx.get_population()
+    q.put((rank, hist, z.cpu().numpy(), K.cpu().numpy()))
+    ctx.close()
+    dist.destroy_process_group()
+
+
+def test_particle_sharded_stages_match_single_context_fp64():
+    """The particles of one problem split over two processes (each its own context with
+    particles_global and particle_base; gloo collectives on the host, so no kernel waits on
+    another process): the all-gathered log-likelihoods give the same beta, evidence and
+    ancestors as one context over all particles, the exchange brings each process the rows
+    of its ancestors, and after two stages of moves (metric and step size from all-reduced
+    sums, added in another order) K agrees exactly and z to 1e-9."""
+    import socket
+
+    import torch.multiprocessing as mp
+
+    from paper_2609_17674_b300 import dist as tdist
+
+    P_glob, stages = 256, 2
+    wl = synth.pulse_workload("shard", 2048, 3, 6, P_glob, 77, n_mut=2)
+    ctx = sampler.open_context(wl, capi.FP64)
+    ctx.init_population()
+    ref = [ctx.run_stage(s, use_graph=False) for s in range(stages)]
+    zr, Kr, _, _ = (x.cpu().numpy() for x in ctx.get_population())
+    ctx.close()
+    mpc = mp.get_context("spawn")
+    q = mpc.Queue()
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    procs = [mpc.Process(target=_particle_shard_worker, args=(r, 2, port, q, P_glob, stages))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in range(2)), key=lambda o: o[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for _, hist, _, _ in out:
+        assert hist[0] == (float(ref[0][0][0]), float(ref[0][1][0]))   # first stage: bitwise
+        assert hist[1][0] == pytest.approx(float(ref[1][0][0]), abs=1e-12)
+        assert hist[1][1] == pytest.approx(float(ref[1][1][0]), rel=1e-11, abs=1e-9)
+    shards = tdist.particle_shards(P_glob, 2)
+    zs = np.concatenate([o[2] for o in out])
+    Ks = np.concatenate([o[3] for o in out])
+    assert [c for _, c in shards] == [o[3].shape[0] for o in out]
+    np.testing.assert_array_equal(Ks, Kr)
+    np.testing.assert_allclose(zs, zr, rtol=1e-9, atol=1e-9)
