@@ -660,9 +660,11 @@ __device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, DF z, const flo
   const DF s = pos ? q : eq;                         // s(z)
   const float ds = __fmul_rn(q.hi, eq.hi);           // s (1 - s)
   if (pr) {
-    const float sc = pos ? eq.hi : q.hi;             // 1 - s
+    // 1 - 2 s = -+(1 - e) q: 1 - e in double-float keeps the prior gradient's relative
+    // precision near z = 0, where (1 - s) - s would cancel to an absolute FP32 error
+    const float om = df_add(DF{1.0f, 0.0f}, df_neg(e)).hi;
     pr->lp = -az.hi - 2.f * log1pf(e.hi);
-    pr->pg = sc - s.hi;
+    pr->pg = (pos ? -om : om) * q.hi;
     pr->pc = 2.f * ds;
   }
   const DF span = df_from(pb.f_span[d]);
@@ -742,6 +744,7 @@ __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& p
   // large |z|, where forming 1 - s by subtraction would cancel
   const float a = fabsf(z);
   const float e = expf(-a);
+  const float om = -expm1f(-a);      // 1 - e, no cancellation near z = 0
   const float q = 1.f / (1.f + e);
   const float s = z >= 0.f ? q : e * q;
   const float sc = z >= 0.f ? e * q : q;
@@ -755,7 +758,7 @@ __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& p
     c.dth = span * ds;
   }
   c.lp = -a - 2.f * log1pf(e);
-  c.pg = sc - s;
+  c.pg = (z >= 0.f ? -om : om) * q;   // 1 - 2 s with full relative precision
   c.pc = 2.f * ds;
   return c;
 }
@@ -1139,10 +1142,14 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
   float* th_lo = th + KD;       // double-float low parts of the pulse centre and width
   // (1) one thread per (component, parameter), parameter-major over a component count
   // padded to 32 so that every warp maps one parameter (no divergence between the
-  // maps of different parameters): element e -> d = e / Kw, k = e % Kw
+  // maps of different parameters): element e -> group g = e / Kw, k = e % Kw.  The group
+  // order starts at parameter 1 so that the amplitude's cheap map comes last: with two
+  // warps and three pulse parameters, centre and width (the double-float maps) fall on
+  // different warps
   const int Kw = (K + 31) & ~31;
   for (int e = threadIdx.x; e < D * Kw; e += blockDim.x) {
-    const int d = e / Kw, k = e - d * Kw;
+    const int grp = e / Kw, k = e - grp * Kw;
+    const int d = grp + 1 < D ? grp + 1 : grp + 1 - D;
     if (k >= K) continue;
     const int i = k * D + d;
     if (leap) {

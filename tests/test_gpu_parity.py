@@ -74,6 +74,40 @@ def test_eval_parity(prec, model, n, kmax, n1, P):
 
 
 @pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+@pytest.mark.parametrize("model", ["pulse", "sinusoid"])
+def test_eval_parity_at_the_component_limit(prec, model):
+    """K_max = 64, the library's limit (components 32..63 live in the second ballot word and
+    the second slot of every lane), with K from 0 to 64 and a ragged tail."""
+    t = torch()
+    wl = _wl(model, 5000, 64, 12, seed=43)
+    z, K = population(wl, 9, 12)
+    K[2:] = [64, 63, 33, 32, 31, 1, 48, 64, 17, 40]
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.6)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.6], t.float64), grad=True)
+    t.cuda.synchronize()
+    res = oracle.Oracle(wl).logl_grad(z, K, 0.6)
+    assert_eval_parity(None, res, lo, ln, lp, g, K, TOL[prec], wl.D)
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_eval_parity_at_the_sample_limit(prec):
+    """N = 2^24 samples, the largest capacity the library accepts (sample indices stay exact
+    in FP32 and 32-bit arithmetic), on a few particles against the oracle."""
+    t = torch()
+    n = 1 << 24
+    wl = synth.pulse_workload("t", n, 3, 4, 4, 44)
+    z, K = population(wl, 10, 4)
+    K[2:] = [3, 4]
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.7)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.7], t.float64), grad=True)
+    t.cuda.synchronize()
+    res = oracle.Oracle(wl).logl_grad(z, K, 0.7)
+    assert_eval_parity(None, res, lo, ln, lp, g, K, TOL[prec], 3)
+    with pytest.raises(capi.TsmcError):   # one sample more than the limit is refused
+        capi.Context(sampler.make_config(wl, prec), [n + 1])
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
 def test_linamp_eval_and_fisher(prec):
     t = torch()
     wl = synth.linamp_workload(n=2100, k=3, P=8)
