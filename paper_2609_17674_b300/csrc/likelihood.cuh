@@ -922,6 +922,55 @@ __device__ __forceinline__ void warp_accumulate(const float (&o)[4], int lane, i
   }
 }
 
+// Warp totals of two components' partial sums a[0..3], b[0..3], one value per group of 4
+// lanes: on return lane l holds the total of (l & 16 ? b : a)[(l >> 2) & 3].  Each total
+// again uses the pairing of the butterfly tree, so it equals warp_sum of that value bit
+// for bit, in 9 shuffles instead of the 12 of two warp_sum4_split calls.
+__device__ __forceinline__ float warp_sum8_split(const float (&a)[4], const float (&b)[4],
+                                                 int lane) {
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+  float k[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+    k[v] = (b4 ? b[v] : a[v]) + __shfl_xor_sync(0xffffffffu, b4 ? a[v] : b[v], 16);
+  float h0 = b3 ? k[2] : k[0], h1 = b3 ? k[3] : k[1];
+  h0 += __shfl_xor_sync(0xffffffffu, b3 ? k[0] : k[2], 8);
+  h1 += __shfl_xor_sync(0xffffffffu, b3 ? k[1] : k[3], 8);
+  float t = b2 ? h1 : h0;
+  t += __shfl_xor_sync(0xffffffffu, b2 ? h0 : h1, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
+// warp_accumulate for two components ka != kb at once (the same sums, row by row, as two
+// warp_accumulate calls, with one reduction's latency instead of two)
+template <int D>
+__device__ __forceinline__ void warp_accumulate2(const float (&oa)[4], const float (&ob)[4],
+                                                 int lane, int ka, int kb, float2* acc) {
+  if (D == 1) {
+    const bool b4 = (lane & 16) != 0;
+    float t = (b4 ? ob[0] : oa[0]) + __shfl_xor_sync(0xffffffffu, b4 ? oa[0] : ob[0], 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((lane & 15) == 0) {
+      const int k = b4 ? kb : ka;
+      float2 a = acc[k];
+      kahan_add(a.x, a.y, t);
+      acc[k] = a;
+    }
+  } else {
+    const float t = warp_sum8_split(oa, ob, lane);
+    const int d = (lane >> 2) & 3;
+    if ((lane & 3) == 0 && d < D) {
+      const int i = (lane & 16 ? kb : ka) * D + d;
+      float2 a = acc[i];
+      kahan_add(a.x, a.y, t);
+      acc[i] = a;
+    }
+  }
+}
+
 __device__ __forceinline__ void load_cf(const float* cf, float (&o)[NCF]) {
   const float4* c4 = reinterpret_cast<const float4*>(cf);
 #pragma unroll
@@ -1333,6 +1382,10 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
     kahan_add(eo_s, eo_c, so);
     kahan_add(en_s, en_c, sn);
     if (GRAD) {
+      // pulses: one component per pass, its partial sums held until the next component's
+      // are ready and both reduced together; sinusoids: two components per pass
+      int kp = -1;
+      float op[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
       for (unsigned long long bits = act64; bits;) {
         const int ka = __ffsll((long long)bits) - 1;
@@ -1345,11 +1398,10 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
             load_cf(cfb + ka * NCF, cf[0]);
             load_cf(cfb + kb * NCF, cf[1]);
             mixed_adj<MODEL, R, 2>(cf, mf, r, o);
-            if (MODEL == SINUSOID && pb.nch == 2)
+            if (pb.nch == 2)
 #pragma unroll
               for (int d = 0; d < 4; ++d) { o[0][d] *= rch; o[1][d] *= rch; }
-            warp_accumulate<D>(o[0], lane, ka, gacc);
-            warp_accumulate<D>(o[1], lane, kb, gacc);
+            warp_accumulate2<D>(o[0], o[1], lane, ka, kb, gacc);
             continue;
           }
         }
@@ -1359,8 +1411,18 @@ __device__ void block_eval_mixed(const ProbDev& pb, const PriorArgs& pa, int K, 
         if (MODEL == SINUSOID && pb.nch == 2)
 #pragma unroll
           for (int d = 0; d < 4; ++d) o[0][d] *= rch;
-        warp_accumulate<D>(o[0], lane, ka, gacc);
+        if (MODEL == SINUSOID) {
+          warp_accumulate<D>(o[0], lane, ka, gacc);
+        } else if (kp < 0) {
+          kp = ka;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) op[d] = o[0][d];
+        } else {
+          warp_accumulate2<D>(op, o[0], lane, kp, ka, gacc);
+          kp = -1;
+        }
       }
+      if (kp >= 0) warp_accumulate<D>(op, lane, kp, gacc);
     }
     if (FISHER) {
       float cw[R];
