@@ -285,9 +285,10 @@ __device__ __forceinline__ void mixed_sub(const float (&cf)[C][NCF], float m, fl
       for (int u = 0; u < C; ++u) {
         const float2 v0 = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del[u],
                                      v00[u]);
-        g[u] = make_float2(ex2a(-v0.x * v0.x), ex2a(-v0.y * v0.y));
-        q[u] = make_float2(ex2a(fminf(-__fmaf_rn(v0.x, cf[u][6], cf[u][7]), 64.0f)),
-                           ex2a(fminf(-__fmaf_rn(v0.y, cf[u][6], cf[u][7]), 64.0f)));
+        const float2 sq = __fmul2_rn(v0, v0);
+        const float2 qa = __ffma2_rn(v0, f2(cf[u][6]), f2(cf[u][7]));
+        g[u] = make_float2(ex2a(-sq.x), ex2a(-sq.y));
+        q[u] = make_float2(ex2a(fminf(-qa.x, 64.0f)), ex2a(fminf(-qa.y, 64.0f)));
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -347,12 +348,12 @@ __device__ __forceinline__ void mixed_adj(const float (&cf)[C][NCF], float m,
     static_assert(C == 1, "pulse components one at a time");
     const bool coarse = cf[0][8] != 0.0f;
     float2 del[C], rho[C], v00[C];
-    float s0[C], s1[C], s2[C];
+    float2 s0[C], s1[C], s2[C];
 #pragma unroll
     for (int u = 0; u < C; ++u) {
       del[u] = f2(cf[u][3]); rho[u] = f2(cf[u][5]);
       v00[u] = f2(dd_axpy(cf[u][1], cf[u][2], cf[u][3], cf[u][4], m));
-      s0[u] = s1[u] = s2[u] = 0.f;
+      s0[u] = s1[u] = s2[u] = f2(0.f);
     }
     if (coarse) {   // C == 1
       float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f);
@@ -368,16 +369,17 @@ __device__ __forceinline__ void mixed_adj(const float (&cf)[C][NCF], float m,
       o[0][0] = a0.x + a0.y; o[0][1] = a1.x + a1.y; o[0][2] = a2.x + a2.y; o[0][3] = 0.f;
       return;
     }
-    const float2 ndel = f2(-cf[0][3]), ndel2 = f2(-2.0f * cf[0][3]), del2 = f2(cf[0][7]);
+    const float2 ndel = f2(-cf[0][3]), del2 = f2(cf[0][7]);
 #pragma unroll
     for (int p = 0; p < R / 16; ++p) {
       float2 v0[C], g[C], q[C], c[C], e[C], fs[C];
 #pragma unroll
       for (int u = 0; u < C; ++u) {
         v0[u] = __ffma2_rn(make_float2((float)(16 * p), (float)(16 * p + 8)), del[u], v00[u]);
-        g[u] = make_float2(ex2a(-v0[u].x * v0[u].x), ex2a(-v0[u].y * v0[u].y));
-        q[u] = make_float2(ex2a(fminf(-__fmaf_rn(v0[u].x, cf[u][6], cf[u][7]), 64.0f)),
-                           ex2a(fminf(-__fmaf_rn(v0[u].y, cf[u][6], cf[u][7]), 64.0f)));
+        const float2 sq = __fmul2_rn(v0[u], v0[u]);
+        const float2 qa = __ffma2_rn(v0[u], f2(cf[u][6]), f2(cf[u][7]));
+        g[u] = make_float2(ex2a(-sq.x), ex2a(-sq.y));
+        q[u] = make_float2(ex2a(fminf(-qa.x, 64.0f)), ex2a(fminf(-qa.y, 64.0f)));
       }
       // running sums over the chunk with p_j = rc_j g_j: c_k = sum_{j<=k} p_j,
       // e_k = sum_{m<=k} c_m, f_k = sum_{m<=k} e_m, so that at its end c = sum p,
@@ -403,20 +405,23 @@ __device__ __forceinline__ void mixed_adj(const float (&cf)[C][NCF], float m,
 #pragma unroll
       for (int u = 0; u < C; ++u) {
         // with w = 8 - j and V = v0 + 8 del (v one past the chunk): v = V - del w, so
-        // sum p v = V c - del e;  sum p v^2 = V^2 c - 2 V del e + del^2 (2 f - e)
+        // sum p v = V c - del e;  sum p v^2 = V (V c - 2 del e) + del^2 (2 f - e), with
+        // V c - 2 del e formed as (sum p v) - del e; the chunk sums are kept per half of
+        // the packed pair and the two halves added at the end
         const float2 V = __ffma2_rn(f2(8.0f), del[u], v0[u]);
-        const float2 c1 = __ffma2_rn(V, c[u], __fmul2_rn(ndel, e[u]));
+        const float2 ne = __fmul2_rn(ndel, e[u]);
+        const float2 c1 = __ffma2_rn(V, c[u], ne);
         const float2 w2 = __ffma2_rn(f2(2.0f), fs[u], make_float2(-e[u].x, -e[u].y));
-        const float2 c2 = __ffma2_rn(V, __ffma2_rn(V, c[u], __fmul2_rn(ndel2, e[u])),
-                                     __fmul2_rn(del2, w2));
-        s0[u] += c[u].x; s0[u] += c[u].y;            // chunks in sample order
-        s1[u] += c1.x; s1[u] += c1.y;
-        s2[u] += c2.x; s2[u] += c2.y;
+        const float2 c2 = __ffma2_rn(V, __fadd2_rn(c1, ne), __fmul2_rn(del2, w2));
+        s0[u] = __fadd2_rn(s0[u], c[u]);
+        s1[u] = __fadd2_rn(s1[u], c1);
+        s2[u] = __fadd2_rn(s2[u], c2);
       }
     }
 #pragma unroll
     for (int u = 0; u < C; ++u) {
-      o[u][0] = s0[u]; o[u][1] = s1[u]; o[u][2] = s2[u]; o[u][3] = 0.f;
+      o[u][0] = s0[u].x + s0[u].y; o[u][1] = s1[u].x + s1[u].y; o[u][2] = s2[u].x + s2[u].y;
+      o[u][3] = 0.f;
     }
   }
 }
