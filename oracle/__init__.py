@@ -41,7 +41,7 @@ class Cfg(C.Structure):
         ("p_nuts", C.c_double), ("p_birth", C.c_double), ("p_death", C.c_double),
         ("lo", C.c_double * 4), ("hi", C.c_double * 4), ("logmask", C.c_uint32),
         ("amp_mean", C.c_double), ("amp_sd", C.c_double), ("fixed_tw", C.c_void_p),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("wrapmask", C.c_uint32),
     ]
 
 
@@ -116,7 +116,7 @@ class Oracle:
                        lo=(C.c_double * 4)(*lo), hi=(C.c_double * 4)(*hi), logmask=wl.logmask,
                        amp_mean=wl.amp_mean, amp_sd=wl.amp_sd,
                        fixed_tw=(self.fixed.ctypes.data if self.fixed is not None else None),
-                       seed=wl.seed)
+                       seed=wl.seed, wrapmask=wl.wrapmask)
         self.data = Data(d=self.d.ctypes.data, n=self.d.shape[0],
                          n1=(pr.n1 if n1 is None else n1), t_origin=pr.t_origin, dt=pr.dt,
                          sigma=pr.sigma)

@@ -85,6 +85,10 @@ static double logaddexp(double a, double b) {
 /* s the logistic function; log-uniform: log theta = log lo + (log hi-log lo) */
 /* s(z).  Either way the prior density of z is the logistic density           */
 /* s(z)(1-s(z)), with d/dz log = 1 - 2 s(z) and -d2/dz2 log = 2 s(1-s).        */
+/* Periodic parameters (wrapmask; a phase, uniform on [lo, hi) with lo and hi */
+/* the same point of the circle): theta = lo + (hi-lo) (z - floor z), so z    */
+/* lives on the circle R/Z, the prior density of z is 1 per period (log 0)    */
+/* and has no gradient or curvature.                                          */
 /* LINAMP (linear-Gaussian test model): identity map, A ~ N(amp_mean, sd^2).  */
 /* The paper samples in BlackJAX's unconstrained space (Sec. 4) and does not  */
 /* state the map; this is the reading used throughout.                        */
@@ -95,8 +99,20 @@ static double logistic(double z) {
   return e / (1.0 + e);
 }
 
+/* z of parameter d whose theta is the prior quantile u in (0, 1): logit(u), or u itself
+ * for a periodic parameter */
+double orc_z_from_u01(const orc_cfg* c, int d, double u) {
+  if (c->wrapmask & (1u << d)) return u;
+  return log(u) - log1p(-u);
+}
+
 void orc_z_to_theta(const orc_cfg* c, int d, double z, double* theta, double* dtheta_dz) {
   if (c->model == ORC_PULSE_LINAMP) { *theta = z; *dtheta_dz = 1.0; return; }
+  if (c->wrapmask & (1u << d)) {
+    *theta = c->lo[d] + (c->hi[d] - c->lo[d]) * (z - floor(z));
+    *dtheta_dz = c->hi[d] - c->lo[d];
+    return;
+  }
   double s = logistic(z);
   double ds = s * (1.0 - s);
   if (c->logmask & (1u << d)) {
@@ -111,7 +127,12 @@ void orc_z_to_theta(const orc_cfg* c, int d, double z, double* theta, double* dt
 }
 
 /* log prior density of one coordinate, its z-gradient and curvature */
-static void log_prior_1(const orc_cfg* c, double z, double* lp, double* g, double* curv) {
+static void log_prior_1(const orc_cfg* c, int d, double z, double* lp, double* g,
+                        double* curv) {
+  if (c->model != ORC_PULSE_LINAMP && (c->wrapmask & (1u << d))) {
+    *lp = 0.0; *g = 0.0; *curv = 0.0;
+    return;
+  }
   if (c->model == ORC_PULSE_LINAMP) {
     double sd = c->amp_sd, dz = (z - c->amp_mean) / sd;
     *lp = -0.5 * dz * dz - log(sd) - 0.5 * log(2.0 * M_PI);
@@ -197,7 +218,7 @@ void orc_logl_grad(const orc_cfg* c, const orc_data* dat, const double* z, int32
   for (int i = 0; i < KD; ++i) {
     orc_z_to_theta(c, i % D, z[i], &theta[i], &dth[i]);
     double lp;
-    log_prior_1(c, z[i], &lp, &pg[i], &pc[i]);
+    log_prior_1(c, (int)(i % D), z[i], &lp, &pg[i], &pc[i]);
     lprior += lp;
   }
   nsum s_old = {0, 0}, s_new = {0, 0};
@@ -281,8 +302,7 @@ void orc_init_population(const orc_cfg* c, int32_t problem, int32_t P, double* z
     K[i] = k;
     for (int j = 0; j < k * D; ++j) {
       draw(c, problem, i, 0, 0, ORC_PU_INIT, 1 + j / 4, w);
-      double u = orc_u01(w[j % 4]);
-      zi[j] = log(u) - log1p(-u);
+      zi[j] = orc_z_from_u01(c, j % D, orc_u01(w[j % 4]));
     }
   }
 }
@@ -342,10 +362,7 @@ void orc_rj_move_q(const orc_cfg* c, const orc_data* dat, int32_t problem, int32
           znew[d] = kde->c[q * D + d] +
                     kde->h[d] * draw_normal(c, problem, i, stage, round, ORC_PU_RJPARAM, 4 + d);
       } else {
-        for (int d = 0; d < D; ++d) {
-          double u = orc_u01(pw[d]);
-          znew[d] = log(u) - log1p(-u);
-        }
+        for (int d = 0; d < D; ++d) znew[d] = orc_z_from_u01(c, d, orc_u01(pw[d]));
       }
       for (int d = 0; d < D; ++d) orc_z_to_theta(c, d, znew[d], &th_new[d], &tmp);
     } else {
@@ -418,6 +435,7 @@ void orc_rj_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32_t
 double orc_log_prior_z(const orc_cfg* c, const double* z) {
   double s = 0.0;
   for (int d = 0; d < c->D; ++d) {
+    if (c->wrapmask & (1u << d)) continue;   /* periodic: density 1 per period */
     const double a = fabs(z[d]);
     s += -a - 2.0 * log1p(exp(-a));
   }
@@ -646,6 +664,10 @@ void orc_nuts_move(const orc_cfg* c, const orc_data* dat, int32_t problem, int32
       if (dot_minv(n, D, minv, rho, pL) <= 0.0 || dot_minv(n, D, minv, rho, pR) <= 0.0) break;
     }
     memcpy(zi, zc, n * 8);
+    /* periodic coordinates leave the transition reduced to one period, z - floor(z), so
+       that positions stay small (the state on the circle is the same) */
+    for (int q = 0; q < n; ++q)
+      if (c->wrapmask & (1u << (q % D))) zi[q] -= floor(zi[q]);
     ll_old[i] = cand_lo; ll_new[i] = cand_ln;
     acc_stat[i] = leaves > 0 ? sum_acc / leaves : 0.0;
     n_leaf_out[i] = leaves;

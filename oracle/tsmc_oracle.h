@@ -54,6 +54,7 @@ typedef struct {
   double amp_mean, amp_sd;        /* LINAMP Gaussian amplitude prior */
   const double* fixed_tw;         /* LINAMP: [kmax][2] fixed (t0, w) */
   uint64_t seed;
+  uint32_t wrapmask;      /* bit d set: parameter d is periodic on [lo, hi) (a phase) */
 } orc_cfg;
 
 typedef struct {
@@ -79,6 +80,7 @@ double orc_u01(uint64_t x);
 
 /* z -> theta map and its derivative for one parameter of type d */
 void orc_z_to_theta(const orc_cfg* c, int d, double z, double* theta, double* dtheta_dz);
+double orc_z_from_u01(const orc_cfg* c, int d, double u);   /* z whose theta is the u-quantile */
 
 /* single template and its parameter derivatives at time t (component k for LINAMP) */
 double orc_template(const orc_cfg* c, int k, const double* theta, double t, double* dh);

@@ -74,6 +74,7 @@ class Workload:
     channels: int = 1         # sinusoids: 2 = channels A and E, data [A samples, E samples]
     resp: tuple = (1.0, 0.0, 1.0, 0.0)   # (r_A, delta_A, r_E, delta_E)
     problem_base: int = 0     # index of problems[0] in a larger set (a shard of it)
+    wrapmask: int = 0         # bit d: parameter d is periodic on [lo, hi) (a phase)
 
     @property
     def D(self) -> int:
@@ -293,6 +294,9 @@ def prior_population(wl: Workload, seed: int, P_total: Optional[int] = None):
     K = rng.integers(wl.kmin, wl.kmax + 1, size=P_total).astype(np.int32)
     u = rng.random((P_total, wl.kmax, wl.D)).clip(1e-12, 1 - 1e-12)
     z = _logit(u)
+    for d in range(wl.D):
+        if wl.wrapmask >> d & 1:          # periodic: z is the position on one period
+            z[..., d] = u[..., d]
     z[np.arange(wl.kmax)[None, :] >= K[:, None]] = 0.0
     return z, K
 
@@ -306,7 +310,10 @@ def theta_to_z(wl: Workload, b: int, theta: np.ndarray) -> np.ndarray:
             u = (np.log(theta[..., d]) - math.log(lo[d])) / (math.log(hi[d]) - math.log(lo[d]))
         else:
             u = (theta[..., d] - lo[d]) / (hi[d] - lo[d])
-        z[..., d] = _logit(np.clip(u, 1e-9, 1 - 1e-9))
+        if wl.wrapmask >> d & 1:
+            z[..., d] = u - np.floor(u)
+        else:
+            z[..., d] = _logit(np.clip(u, 1e-9, 1 - 1e-9))
     return z
 
 
