@@ -111,6 +111,16 @@ typedef struct {
                                holds particles [particle_base, particle_base + particles) */
   int32_t particle_base;  /* global index of the context's first particle (Philox counter
                              word 0 = particle_base + local index), 0 unless sharded */
+  uint32_t wrap_mask;     /* bit d set: parameter d is periodic on [lo_d, hi_d), a phase such
+                             as the sinusoid phi0 ~ U[0, 2 pi) of Sec. 5.2 (bit 3):
+                             theta = lo + (hi - lo)(z - floor z), so z lives on a circle, its
+                             prior density is flat (log prior 0, no gradient or curvature),
+                             prior draws and births take z = u in (0, 1), and every NUTS
+                             transition leaves the coordinate reduced to z - floor z.  0: every
+                             parameter uses the logit map.  Bits at or above the model's D, a
+                             bit also set in a problem's logmask (tsmc_set_problem), the LINAMP
+                             model and birth_proposal = 1 (whose kernel density is not
+                             periodic) give TSMC_EINVAL */
 } tsmc_config;
 
 /* Opaque context: created by tsmc_create, released by tsmc_destroy. */

@@ -77,6 +77,7 @@ class Config(C.Structure):
         ("channels", C.c_int32), ("response", C.c_double * 4),
         ("problem_base", C.c_int32), ("fused_rounds", C.c_int32),
         ("particles_global", C.c_int32), ("particle_base", C.c_int32),
+        ("wrap_mask", C.c_uint32),
     ]
 
 

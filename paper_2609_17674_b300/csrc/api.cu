@@ -136,6 +136,10 @@ tsmc_status check_cfg(const tsmc_config* cfg) {
       if (!std::isfinite(cfg->response[q])) return TSMC_EINVAL;
     if (!(cfg->response[0] > 0.0) || !(cfg->response[2] > 0.0)) return TSMC_EINVAL;
   }
+  if (cfg->wrap_mask != 0) {
+    if (cfg->model == TSMC_PULSE_LINAMP || cfg->birth_proposal == 1) return TSMC_EINVAL;
+    if (cfg->wrap_mask >> model_dim(cfg->model)) return TSMC_EINVAL;
+  }
   return TSMC_OK;
 }
 
@@ -745,7 +749,10 @@ tsmc_status tsmc_set_problem(tsmc_ctx* ctx, int32_t problem, const double* d_hos
   pd.dt = dt;
   pd.sigma = sigma;
   pd.inv_s2 = 1.0 / (sigma * sigma);
+  if (logmask & c->cfg.wrap_mask)
+    return fail(c, TSMC_EINVAL, "a periodic parameter cannot be log-uniform");
   pd.logmask = logmask;
+  pd.wrapmask = c->cfg.wrap_mask;
   pd.done = 0;
   for (int d = 0; d < 4; ++d) {
     const bool used = d < c->D && c->cfg.model != TSMC_PULSE_LINAMP;

@@ -89,7 +89,8 @@ struct ProbDev {
   // E at the same times; channel c sees resp[2c] A cos(phi(t) + resp[2c+1]).  nch = 1: one
   // channel, nc = n.
   int64_t nc;
-  int32_t nch, pad_;
+  int32_t nch;
+  uint32_t wrapmask; // bit d: parameter d periodic on [lo, hi): theta = lo + span (z - floor z)
   double resp[4];
   float f_resp[4];
   float2 f_is2;      // 1/sigma^2 as double-float

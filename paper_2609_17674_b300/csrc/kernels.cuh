@@ -178,10 +178,12 @@ __global__ void k_init(KParams kp, int64_t Ptot) {
   int k = kp.kmin + (int)floor(__dmul_rn(u01(w.w[0]), (double)(kp.kmax - kp.kmin + 1)));
   if (k > kp.kmax) k = kp.kmax;
   kp.K[gi] = k;
+  const uint32_t wrap = kp.probs[prob].wrapmask;
   for (int j = 0; j < k * kp.D; ++j) {
     if ((j & 3) == 0) w = draw(kp.seed, pkey, li, 0, 0, PU_INIT, 1 + (uint64_t)(j >> 2));
     const double u = u01(w.w[j & 3]);
-    z[j] = log(u) - log1p(-u);
+    // theta at the prior quantile u: logit(u), or u itself on a periodic coordinate
+    z[j] = (wrap >> (j % kp.D) & 1u) ? u : log(u) - log1p(-u);
   }
 }
 
@@ -300,7 +302,7 @@ __device__ void rj_particle(const KParams& kp, int64_t gi, int round, int32_t* o
       } else {
         for (int d = 0; d < D; ++d) {
           const double u = u01(pw.w[d]);
-          s_znew[d] = log(u) - log1p(-u);
+          s_znew[d] = (pb.wrapmask >> d & 1u) ? u : log(u) - log1p(-u);
         }
       }
     } else if (move == 2) {
@@ -796,7 +798,9 @@ __global__ void TSMC_PARTICLE_BOUNDS k_nuts(KParams kp, int round, NutsOut out, 
   }
   if (warp == 0) {
     double* zw = kp.z + gi * (int64_t)kd;
-    for (int i = lane; i < n; i += 32) zw[i] = zc[i];
+    // periodic coordinates leave the transition reduced to one period
+    for (int i = lane; i < n; i += 32)
+      zw[i] = (pb.wrapmask >> (i % D) & 1u) ? __dadd_rn(zc[i], -floor(zc[i])) : zc[i];
     if (lane == 0) {
       const int leaves = s_flag[3];
       kp.ll_old[gi] = s_ctl[3];
@@ -1096,9 +1100,14 @@ __device__ void nuts_particle_mixed(const KParams& kp, int64_t gi, int round, Nu
     l = 0;
   }
   if (warp == 0) {
-    if (moved) {   // an unmoved particle keeps its FP64 coordinates exactly
-      double* zw = kp.z + gi * (int64_t)kd;
-      for (int i = lane; i < n; i += 32) zw[i] = to_double(zc[i]);
+    // an unmoved particle keeps its FP64 coordinates exactly; periodic coordinates leave
+    // the transition reduced to one period either way
+    double* zw = kp.z + gi * (int64_t)kd;
+    for (int i = lane; i < n; i += 32) {
+      const bool wr = pb.wrapmask >> (i % D) & 1u;
+      if (!moved && !wr) continue;
+      const double v = moved ? to_double(zc[i]) : zw[i];
+      zw[i] = wr ? __dadd_rn(v, -floor(v)) : v;
     }
     if (lane == 0) {
       const int leaves = s_flag[3];

@@ -44,6 +44,13 @@ __device__ __forceinline__ void coord(const ProbDev& pb, const PriorArgs& pa, in
     pc = 1.0 / (sd * sd);
     return;
   }
+  if (pb.wrapmask & (1u << d)) {   // periodic: theta = lo + span (z - floor z), flat prior
+    const double span = __dadd_rn(pb.hi[d], -pb.lo[d]);
+    th = __dadd_rn(pb.lo[d], __dmul_rn(span, __dadd_rn(z, -floor(z))));
+    dth = span;
+    lp = 0.0; pg = 0.0; pc = 0.0;
+    return;
+  }
   const double s = logistic(z);
   const double ds = __dmul_rn(s, __dadd_rn(1.0, -s));
   if (pb.logmask & (1u << d)) {
@@ -591,6 +598,16 @@ __device__ __forceinline__ DF df_mul_f(DF a, float b) {
 
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
 
+// fractional part of a double-float coordinate, in [0, 1); a non-finite coordinate gives 0
+// (an FP64 coordinate beyond 2^52 has no fractional part either)
+__device__ __forceinline__ DF df_frac(DF z) {
+  if (!isfinite(z.hi)) return DF{0.f, 0.f};
+  DF f = two_sum(z.hi - floorf(z.hi), z.lo);   // the first difference is exact
+  if (f.hi < 0.f) f = df_add(f, DF{1.f, 0.f});
+  else if (f.hi >= 1.f) f = df_add(f, DF{-1.f, 0.f});
+  return f;
+}
+
 // 1 / a (a > 0): FP32 reciprocal refined by one Newton step in double-float
 __device__ __forceinline__ DF df_recip(DF a) {
   const float q = __frcp_rn(a.hi);
@@ -657,6 +674,12 @@ struct Coord32 { float th, dth, lp, pg, pc; };
 // e^{-|z|} and 1/(1+e)
 __device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, DF z, const float2* tab,
                                        float& dth, Coord32* pr = nullptr) {
+  if (pb.wrapmask & (1u << d)) {   // periodic, flat prior
+    if (pr) { pr->lp = 0.f; pr->pg = 0.f; pr->pc = 0.f; }
+    const DF span = df_from(pb.f_span[d]);
+    dth = span.hi;
+    return df_add(df_from(pb.f_off[d]), df_mul(span, df_frac(z)));
+  }
   const bool pos = z.hi >= 0.f;
   const DF az = pos ? z : df_neg(z);
   const DF e = df_exp(df_neg(az), tab);              // e^{-|z|}
@@ -735,8 +758,16 @@ __device__ __forceinline__ void finish_fisher(int prec, const double* th, const 
 // below the path's tolerance: amplitudes, widths, frequency derivative, phase)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& pa, int d, float z) {
+__device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& pa, int d, DF zz) {
+  const float z = zz.hi;
   Coord32 c;
+  if (pa.model != PULSE_LINAMP && (pb.wrapmask & (1u << d))) {   // periodic, flat prior
+    const DF f = df_frac(zz);
+    c.th = pb.f_off[d].x + pb.f_span[d].x * (f.hi + f.lo);
+    c.dth = pb.f_span[d].x;
+    c.lp = 0.f; c.pg = 0.f; c.pc = 0.f;
+    return c;
+  }
   if (pa.model == PULSE_LINAMP) {
     const float sd = (float)pa.amp_sd, dz = (z - (float)pa.amp_mean) / sd;
     c.th = z; c.dth = 1.f;
@@ -773,6 +804,11 @@ __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& p
 // rounding of the log-space argument of a log-uniform map, would move the template
 // by more than the path's tolerance (tails of narrow pulses, far end of the grid).
 __device__ __forceinline__ double theta64(const ProbDev& pb, int d, double z, double& dth) {
+  if (pb.wrapmask & (1u << d)) {
+    const double span = pb.hi[d] - pb.lo[d];
+    dth = span;
+    return pb.lo[d] + span * (z - floor(z));
+  }
   const double e = exp(-fabs(z));
   const double q = 1.0 / (1.0 + e);
   const double s = z >= 0.0 ? q : e * q;
@@ -1223,7 +1259,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       pcv[i] = c.pc;
       lp += c.lp;
     } else {
-      const Coord32 c = coord32(pb, pa, d, to_df(zi).hi);
+      const Coord32 c = coord32(pb, pa, d, to_df(zi));
       th[i] = c.th;
       dth[i] = c.dth;
       pgv[i] = c.pg;

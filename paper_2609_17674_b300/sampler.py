@@ -30,7 +30,8 @@ def make_config(wl: Workload, precision: int = capi.MIXED, threads: int = 0,
                        pulse_window=pulse_window if precision == capi.MIXED else 0,
                        problem_base=wl.problem_base, fused_rounds=fused_rounds,
                        particle_base=particle_shard[0] if particle_shard else 0,
-                       particles_global=particle_shard[1] if particle_shard else 0)
+                       particles_global=particle_shard[1] if particle_shard else 0,
+                       wrap_mask=wl.wrapmask)
 
 
 def open_context(wl: Workload, precision=capi.MIXED, n_use=None, n_capacity=None, threads=0,

@@ -90,6 +90,32 @@ def test_particle_shard_configuration_rules():
     assert status(fused_rounds=2) == capi.EINVAL
 
 
+def test_periodic_parameter_configuration_rules():
+    """wrap_mask: bits below the model's D only; not with the linear-amplitude model or the
+    population birth proposal (its kernel density is not periodic)."""
+    L = capi.lib()
+    cap = np.array([4096], dtype=np.int64)
+    nb = C.c_size_t(0)
+
+    def status(wl, **kw):
+        cfg = make_config(wl, capi.MIXED)
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        return L.tsmc_workspace_bytes(C.byref(cfg), cap.ctypes.data, C.byref(nb))
+
+    ws = synth.sinusoid_workload("t", 4096, 3, 8, 64, 1)
+    wp = synth.pulse_workload("t", 4096, 3, 8, 64, 1)
+    assert status(ws, wrap_mask=0b1000) == capi.OK
+    assert status(ws, wrap_mask=0b1111) == capi.OK
+    assert status(ws, wrap_mask=0b10000) == capi.EINVAL        # sinusoids have 4 parameters
+    assert status(wp, wrap_mask=0b100) == capi.OK
+    assert status(wp, wrap_mask=0b1000) == capi.EINVAL         # pulses have 3
+    assert status(ws, wrap_mask=0b1000, birth_proposal=1, birth_prior_weight=0.2) == capi.EINVAL
+    assert status(synth.linamp_workload(), wrap_mask=1) == capi.EINVAL
+    ws.wrapmask = 0b1000
+    assert make_config(ws, capi.MIXED).wrap_mask == 0b1000
+
+
 def test_create_rejects_misaligned_workspace_without_device_work():
     L = capi.lib()
     wl = synth.pulse_n1024_k3()
