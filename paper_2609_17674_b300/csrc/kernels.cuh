@@ -1103,11 +1103,14 @@ __device__ void nuts_particle_mixed(const KParams& kp, int64_t gi, int round, Nu
     // an unmoved particle keeps its FP64 coordinates exactly; periodic coordinates leave
     // the transition reduced to one period either way
     double* zw = kp.z + gi * (int64_t)kd;
-    for (int i = lane; i < n; i += 32) {
-      const bool wr = pb.wrapmask >> (i % D) & 1u;
-      if (!moved && !wr) continue;
-      const double v = moved ? to_double(zc[i]) : zw[i];
-      zw[i] = wr ? __dadd_rn(v, -floor(v)) : v;
+    const uint32_t wm = pb.wrapmask;
+    if (moved) {
+      for (int i = lane; i < n; i += 32) zw[i] = to_double(zc[i]);
+    }
+    if (wm) {
+      __syncwarp();
+      for (int i = lane; i < n; i += 32)
+        if (wm >> (i % D) & 1u) zw[i] = __dadd_rn(zw[i], -floor(zw[i]));
     }
     if (lane == 0) {
       const int leaves = s_flag[3];

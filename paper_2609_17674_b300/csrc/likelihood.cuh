@@ -672,13 +672,16 @@ struct Coord32 { float th, dth, lp, pg, pc; };
 // theta in double-float from a double-float coordinate z; with pr != nullptr also the log
 // prior density of z and its first two derivatives (lp, pg, pc of Coord32) from the same
 // e^{-|z|} and 1/(1+e)
+template <bool WRAP = true>
 __device__ __forceinline__ DF theta_df(const ProbDev& pb, int d, DF z, const float2* tab,
                                        float& dth, Coord32* pr = nullptr) {
-  if (pb.wrapmask & (1u << d)) {   // periodic, flat prior
-    if (pr) { pr->lp = 0.f; pr->pg = 0.f; pr->pc = 0.f; }
-    const DF span = df_from(pb.f_span[d]);
-    dth = span.hi;
-    return df_add(df_from(pb.f_off[d]), df_mul(span, df_frac(z)));
+  if constexpr (WRAP) {
+    if (pb.wrapmask & (1u << d)) {   // periodic, flat prior
+      if (pr) { pr->lp = 0.f; pr->pg = 0.f; pr->pc = 0.f; }
+      const DF span = df_from(pb.f_span[d]);
+      dth = span.hi;
+      return df_add(df_from(pb.f_off[d]), df_mul(span, df_frac(z)));
+    }
   }
   const bool pos = z.hi >= 0.f;
   const DF az = pos ? z : df_neg(z);
@@ -758,15 +761,19 @@ __device__ __forceinline__ void finish_fisher(int prec, const double* th, const 
 // below the path's tolerance: amplitudes, widths, frequency derivative, phase)
 // ---------------------------------------------------------------------------
 
+// WRAP = false: the problem has no periodic parameter (the branch is compiled out)
+template <bool WRAP = true>
 __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& pa, int d, DF zz) {
   const float z = zz.hi;
   Coord32 c;
-  if (pa.model != PULSE_LINAMP && (pb.wrapmask & (1u << d))) {   // periodic, flat prior
-    const DF f = df_frac(zz);
-    c.th = pb.f_off[d].x + pb.f_span[d].x * (f.hi + f.lo);
-    c.dth = pb.f_span[d].x;
-    c.lp = 0.f; c.pg = 0.f; c.pc = 0.f;
-    return c;
+  if constexpr (WRAP) {
+    if (pa.model != PULSE_LINAMP && (pb.wrapmask & (1u << d))) {   // periodic, flat prior
+      const DF f = df_frac(zz);
+      c.th = pb.f_off[d].x + pb.f_span[d].x * (f.hi + f.lo);
+      c.dth = pb.f_span[d].x;
+      c.lp = 0.f; c.pg = 0.f; c.pc = 0.f;
+      return c;
+    }
   }
   if (pa.model == PULSE_LINAMP) {
     const float sd = (float)pa.amp_sd, dz = (z - (float)pa.amp_mean) / sd;
@@ -803,11 +810,14 @@ __device__ __forceinline__ Coord32 coord32(const ProbDev& pb, const PriorArgs& p
 // (pulse centre and width, sinusoid frequency): their FP32 rounding, or the FP32
 // rounding of the log-space argument of a log-uniform map, would move the template
 // by more than the path's tolerance (tails of narrow pulses, far end of the grid).
+template <bool WRAP = true>
 __device__ __forceinline__ double theta64(const ProbDev& pb, int d, double z, double& dth) {
-  if (pb.wrapmask & (1u << d)) {
-    const double span = pb.hi[d] - pb.lo[d];
-    dth = span;
-    return pb.lo[d] + span * (z - floor(z));
+  if constexpr (WRAP) {
+    if (pb.wrapmask & (1u << d)) {
+      const double span = pb.hi[d] - pb.lo[d];
+      dth = span;
+      return pb.lo[d] + span * (z - floor(z));
+    }
   }
   const double e = exp(-fabs(z));
   const double q = 1.0 / (1.0 + e);
@@ -1222,20 +1232,21 @@ struct LeapPre {
   float de_c;
 };
 
-template <int MODEL, int R, typename ZT>
-__device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const ZT* z,
-                                  EvalSmem& sm, const LeapPre<ZT>* leap = nullptr) {
+// (1) of the mixed setup: one thread per (component, parameter), parameter-major over a
+// component count padded to 32 so that every warp maps one parameter (no divergence
+// between the maps of different parameters): element e -> group g = e / Kw, k = e % Kw.
+// The group order starts at parameter 1 so that the amplitude's cheap map comes last: with
+// two warps and three pulse parameters, centre and width (the double-float maps) fall on
+// different warps.  WRAP = false for problems without periodic parameters.  Returns the
+// thread's share of the log prior.
+template <int MODEL, bool WRAP, typename ZT>
+__device__ __forceinline__ float setup_elements(const ProbDev& pb, const PriorArgs& pa, int K,
+                                                const ZT* z, EvalSmem& sm,
+                                                const LeapPre<ZT>* leap) {
   constexpr int D = model_d<MODEL>();
   float lp = 0.f;
   float *th = sm.fth(), *dth = sm.fdth(), *pgv = sm.fpg(), *pcv = sm.fpc();
-  const int KD = K * D;
-  float* th_lo = th + KD;       // double-float low parts of the pulse centre and width
-  // (1) one thread per (component, parameter), parameter-major over a component count
-  // padded to 32 so that every warp maps one parameter (no divergence between the
-  // maps of different parameters): element e -> group g = e / Kw, k = e % Kw.  The group
-  // order starts at parameter 1 so that the amplitude's cheap map comes last: with two
-  // warps and three pulse parameters, centre and width (the double-float maps) fall on
-  // different warps
+  float* th_lo = th + K * D;    // double-float low parts of the pulse centre and width
   const int Kw = (K + 31) & ~31;
   for (int e = threadIdx.x; e < D * Kw; e += blockDim.x) {
     const int grp = e / Kw, k = e - grp * Kw;
@@ -1251,7 +1262,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
     if (MODEL == PULSE && d > 0) {
       // centre and width to ~1e-12 relative in double-float (FP32 pipe, no FP64)
       Coord32 c;
-      const DF t = theta_df(pb, d, to_df(zi), sm.exptab, c.dth, &c);
+      const DF t = theta_df<WRAP>(pb, d, to_df(zi), sm.exptab, c.dth, &c);
       th[i] = t.hi;
       th_lo[i] = t.lo;
       dth[i] = c.dth;
@@ -1259,7 +1270,7 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       pcv[i] = c.pc;
       lp += c.lp;
     } else {
-      const Coord32 c = coord32(pb, pa, d, to_df(zi));
+      const Coord32 c = coord32<WRAP>(pb, pa, d, to_df(zi));
       th[i] = c.th;
       dth[i] = c.dth;
       pgv[i] = c.pg;
@@ -1267,11 +1278,23 @@ __device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K,
       lp += c.lp;
       if (MODEL == SINUSOID && d == 1) {   // frequency in FP64 for the phase constants
         double d1;
-        sm.wacc[i / D] = theta64(pb, 1, to_double(zi), d1);   // scratch until the sample loop
+        sm.wacc[i / D] = theta64<WRAP>(pb, 1, to_double(zi), d1);   // scratch until the sample loop
         dth[i] = (float)d1;
       }
     }
   }
+  return lp;
+}
+
+template <int MODEL, int R, typename ZT>
+__device__ float eval_setup_mixed(const ProbDev& pb, const PriorArgs& pa, int K, const ZT* z,
+                                  EvalSmem& sm, const LeapPre<ZT>* leap = nullptr) {
+  constexpr int D = model_d<MODEL>();
+  const float* th = sm.fth();
+  const float* th_lo = th + K * D;   // double-float low parts of the pulse centre and width
+  // (1) the coordinate maps (and the leapfrog position step), element by element
+  const float lp = pb.wrapmask ? setup_elements<MODEL, true, ZT>(pb, pa, K, z, sm, leap)
+                               : setup_elements<MODEL, false, ZT>(pb, pa, K, z, sm, leap);
   __syncthreads();
   // (2) one thread per component: path constants
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
