@@ -39,7 +39,7 @@ FP32_LANES_PER_SM = 128
 # (profiles/k_nuts_mixed_pulse_n16384_p1024.md); traffic scales with the particle count (z
 # rows in and out; the samples stay in L2).  None when the kernel has changed since the
 # capture.
-NUTS_DRAM_BYTES_PER_PARTICLE = 568.5
+NUTS_DRAM_BYTES_PER_PARTICLE = 579.0
 NUTS_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of a 1024-particle launch, scaled per "
                      "particle (profiles/k_nuts_mixed_pulse_n16384_p1024.md)")
 
