@@ -201,3 +201,26 @@ def test_phase_posterior_crosses_the_seam():
     m = np.mean(np.exp(1j * phi))
     sd = np.sqrt(-2.0 * np.log(np.abs(m)))              # circular standard deviation
     assert abs(np.angle(m * np.exp(-1j * th[0, PHASE]))) <= 3 * sd, (np.angle(m), sd)
+
+
+@pytest.mark.parametrize("prec", [capi.FP64, capi.MIXED])
+def test_two_channel_eval_parity_with_periodic_phase(prec):
+    """Channels A and E add their response phase to phi0; with the periodic map phi0 comes
+    from the fraction of z first."""
+    t = torch()
+    wl = synth.ae_workload("t", 4096, 3, 5, 24, 41, noise=True)
+    wl.wrapmask = WRAP
+    z, K = population(wl, 5, 24)
+    zt = synth.theta_to_z(wl, 0, wl.problems[0].truth)
+    for i in range(2, 24, 2):
+        k = min(K[i], 3)
+        K[i] = k
+        z[i, :k] = zt[:k] + 0.01 * np.random.default_rng(i).standard_normal((k, 4))
+    z = _spread(z, 6)
+    z[np.arange(wl.kmax)[None, :] >= K[:, None]] = 0.0
+    ctx, zd, Kd = context_with_population(wl, prec, z, K, 0.37)
+    lo, ln, lp, g, _ = ctx.eval(zd, Kd, dev_tensor([0.37], t.float64), grad=True)
+    t.cuda.synchronize()
+    ora = oracle.Oracle(wl)
+    res = ora.logl_grad(z, K, 0.37)
+    assert_eval_parity(ora, res, lo, ln, lp, g, K, TOL[prec], wl.D)
