@@ -224,3 +224,24 @@ def test_two_channel_eval_parity_with_periodic_phase(prec):
     ora = oracle.Oracle(wl)
     res = ora.logl_grad(z, K, 0.37)
     assert_eval_parity(ora, res, lo, ln, lp, g, K, TOL[prec], wl.D)
+
+
+def test_rj_move_with_periodic_phase_mixed_agrees():
+    t = torch()
+    wl = _wl(P=512)
+    z, K = population(wl, 12, wl.P)
+    z = _spread(z, 3)
+    z[np.arange(wl.kmax)[None, :] >= K[:, None]] = 0.0
+    beta = 0.3
+    ora = oracle.Oracle(wl)
+    ctx, _, _ = context_with_population(wl, capi.MIXED, z, K, beta)
+    r = ora.logl_grad(z, K, beta)
+    lo, ln = r["ll_old"].copy(), r["ll_new"].copy()
+    zo, Ko = z.copy(), K.copy()
+    out_o = ora.rj_move(2, 1, beta, zo, Ko, lo, ln)
+    outd = t.zeros(wl.P, dtype=t.int32, device="cuda")
+    ctx.rj_move(2, 1, outd)
+    assert np.mean(outd.cpu().numpy() == out_o) > 0.99
+    zg = ctx.get_population()[0].cpu().numpy()
+    same = outd.cpu().numpy() == out_o
+    assert np.array_equal(zg[same][..., PHASE], zo[same][..., PHASE])
