@@ -63,9 +63,12 @@ def test_pulse_n16384_k20_full_smc_reaches_the_injection_likelihood():
     assert np.median(lp) >= lt - p / 2, (np.median(lp), lt)
 
 
-def test_gb_band_n262144_k10_full_smc_recovers_the_injection():
+@pytest.mark.parametrize("periodic_phase", [False, True])
+def test_gb_band_n262144_k10_full_smc_recovers_the_injection(periodic_phase):
     torch()
     wl = synth.gb_band_k10(P=1024)           # N = 2^18 at 15 s, K_true = 10, K_max = 30
+    if periodic_phase:
+        wl.wrapmask = 1 << 3                 # phi0 on the circle
     out, z, K = _run(wl, max_stages=400)
     assert out["beta"][-1][0] == 1.0
     pr = wl.problems[0]
@@ -84,6 +87,16 @@ def test_gb_band_n262144_k10_full_smc_recovers_the_injection():
     T = pr.n * pr.dt
     dev = np.abs(f.mean(0) - np.sort(pr.truth[:, 1]))
     assert np.all(dev <= 3 * f.std(0) + 0.1 / T), (dev, f.std(0))
+    if periodic_phase:
+        # phases of the same components (labels ordered by frequency), on the circle
+        order = np.argsort(lo[1] + (hi[1] - lo[1]) / (1.0 + np.exp(-z[sel, :kt, 1])), axis=1)
+        u = np.take_along_axis(z[sel, :kt, 3], order, 1)
+        ph = 2 * np.pi * (u - np.floor(u))
+        m = np.mean(np.exp(1j * ph), axis=0)
+        sd = np.sqrt(-2.0 * np.log(np.abs(m)))
+        tr = pr.truth[np.argsort(pr.truth[:, 1]), 3]
+        err = np.abs(np.angle(m * np.exp(-1j * tr)))
+        assert np.all(err <= 3 * sd + 0.05), (err, sd)
 
 
 def test_batched_gb_bands_full_smc_reach_their_injections():
