@@ -245,3 +245,13 @@ def test_rj_move_with_periodic_phase_mixed_agrees():
     zg = ctx.get_population()[0].cpu().numpy()
     same = outd.cpu().numpy() == out_o
     assert np.array_equal(zg[same][..., PHASE], zo[same][..., PHASE])
+
+
+def test_periodic_parameter_cannot_be_log_uniform():
+    wl = _wl(P=8)
+    ctx = sampler.open_context(wl, capi.MIXED)
+    pr = wl.problems[0]
+    with pytest.raises(capi.TsmcError):      # bit 3 both periodic and log-uniform
+        ctx.set_problem(0, pr.d, pr.t_origin, pr.dt, pr.sigma, (1.0, 1.0, 1.0, 0.1),
+                        (2.0, 2.0, 2.0, 2 * np.pi), wl.logmask | WRAP)
+    ctx.set_problem(0, pr.d, pr.t_origin, pr.dt, pr.sigma, pr.lo, pr.hi, wl.logmask)
