@@ -15,7 +15,8 @@
  *     library never allocates device memory: all state lives in the workspace
  *     the caller passes to tsmc_create.
  *   - Coordinates z are FP64, row-major [n_problems * P][kmax][D], unconstrained
- *     (logit) coordinates; D = 3 (pulse: A, t0, w), 4 (sinusoid: A, f, fdot,
+ *     (logit) coordinates, or positions on a circle for the parameters set in
+ *     tsmc_config.wrap_mask; D = 3 (pulse: A, t0, w), 4 (sinusoid: A, f, fdot,
  *     phi0), 1 (linear-amplitude test model).  Rows k >= K_p are ignored on
  *     input and written as zero.
  *   - Particle index = problem * P + local index.
@@ -154,8 +155,9 @@ tsmc_status tsmc_set_problem(tsmc_ctx* ctx, int32_t problem, const double* d_hos
 /* LINAMP only: fixed (t0, w) per component, host [kmax][2]. */
 tsmc_status tsmc_set_fixed_components(tsmc_ctx* ctx, const double* tw_host);
 
-/* Prior start (Sec. 4 step 1): K ~ U{kmin..kmax}, z ~ logistic (theta from its prior);
- * beta = 0, log Z = 0, step size eps_0 = 0.5 (kmax D)^(-1/4), unit metric. */
+/* Prior start (Sec. 4 step 1): K ~ U{kmin..kmax}, z ~ logistic (theta from its prior;
+ * z ~ U(0, 1) for a periodic parameter); beta = 0, log Z = 0, step size
+ * eps_0 = 0.5 (kmax D)^(-1/4), unit metric. */
 tsmc_status tsmc_init_population(tsmc_ctx* ctx);
 
 /* Posterior start / resume: population from device arrays, beta and log Z per problem. */
